@@ -1,0 +1,139 @@
+"""Pins of the oracle's nonlinear solvers (Algorithms 1-3) against closed forms and invariants."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import am, fe
+from oracle.problem import Problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def test_golden_constants():
+    g = _golden()
+    assert abs(fe.Material(model="AT1").cw - g["c_w"]["AT1"]["value"]) < 1e-15
+    assert abs(fe.Material(model="AT2").cw - g["c_w"]["AT2"]["value"]) < 1e-15
+    tc = W.bar_critical_displacement(1.0, 1.0, 0.3, 1.0, 0.05)
+    assert abs(tc - g["bar_tc_plane_strain"]["value"]) < 5e-5
+    dtc = W.thermal_critical_jump(1.0, 0.3, 1.0, 3.0 / 1024.0, 1.0)
+    assert abs(dtc - g["thermal_dTc_plane_strain"]["value"]) < 5e-3
+
+
+def test_bar_config_elastic_phase_and_critical_step():
+    """Traction of a bar, 128x16 right mesh, AT1 (Section 4.2, plane-strain reading of t_c):
+    alpha == 0 and E = 1/2 E' (t/L)^2 L H for t < t_c; first damage at step 14 of 20."""
+    w = W.bar()
+    p = Problem(w)
+    Ep = w.E / (1 - w.nu ** 2)
+    tc = W.bar_critical_displacement(w.lx, w.E, w.nu, w.Gc, w.ell)
+    first_damaged = None
+    for k, (t, dT) in enumerate(w.loads[:14], start=1):
+        r = am.load_step(p, t, dT, omega=1.0, tol=1e-8)
+        assert r["status"] == "converged"
+        if t < tc:
+            assert p.alpha.max() == 0.0
+            el = r["energy"][0]
+            np.testing.assert_allclose(el, 0.5 * (1 + w.k_ell) * Ep * (t / w.lx) ** 2 * w.lx * w.ly,
+                                       rtol=1e-10)
+        elif first_damaged is None and p.alpha.max() > 0:
+            first_damaged = k
+    assert first_damaged == 14
+
+
+def test_1d_critical_stress():
+    """nu = 0 bar without damage Dirichlet data is one-dimensional: homogeneous damage appears
+    exactly when E t / L exceeds sigma_c = sqrt(3 Gc E / (8 ell)) (Section 4, first formula)."""
+    w = W.bar(nx=16, ny=2, nu=0.0)
+    w.fixed = {"left": {"ux": 0.0}, "right": {"ux": 1.0}}
+    sc = np.sqrt(3 * w.Gc * w.E / (8 * w.ell))
+    for factor, damaged in ((0.999, False), (1.001, True)):
+        p = Problem(w)
+        t = factor * sc * w.lx / w.E
+        am.load_step(p, t, 0.0, omega=1.0, tol=1e-12)
+        assert (p.alpha.max() > 0) == damaged
+        if damaged:  # homogeneous stationary point: alpha = 1 - 3 Gc / (8 ell E eps^2)
+            np.testing.assert_allclose(p.alpha, 1 - 3 * w.Gc / (8 * w.ell * w.E * (t / w.lx) ** 2),
+                                       rtol=1e-8)
+
+
+@pytest.mark.parametrize("ratio", [10, 20])
+def test_developed_profile_surface_energy(ratio):
+    """A fully developed AT1 crack (alpha = 1 on one column, u = 0) costs Gc per unit length,
+    up to an O(h/ell) discretization error; the profile is (1 - |x|/(2 ell))^2."""
+    ell = 0.05
+    nx = int(round(1.0 / (ell / ratio)))
+    nx += nx % 2
+    w = W.Workload(name="profile", kind="right", nx=nx, ny=2, x0=-0.5, y0=0, lx=1.0,
+                   ly=1.0 / nx * 2, ell=ell, alpha_boxes=[(nx, nx, 0, 4, 1.0)])
+    p = Problem(w)
+    a, info = am.solve_alpha(p, np.zeros((p.mesh.n_nodes, 2)), p.alpha.copy(), 0.0)
+    surf = fe.energy(p.mat, p.geo, np.zeros((p.mesh.n_nodes, 2)), a)[1]
+    rel = surf / (w.Gc * w.ly) - 1
+    assert 0 < rel < 1.0 / ratio  # converges from above at O(h/ell)
+    x = p.mesh.xy[:, 0]
+    prof = np.clip(1 - np.abs(x) / (2 * ell), 0, None) ** 2
+    assert np.abs(a - prof).max() < 2.0 / ratio
+
+
+def test_oram_energy_monotone_bounds_irreversibility():
+    """For any omega in (0, 2) each ORAM sweep cannot raise the energy (each block step moves
+    along the segment towards the exact block minimizer); alpha stays in [alpha_prev, 1]."""
+    w = W.notched_square(n=16, n_steps=10, t_max=1.2)
+    for omega in (1.0, 1.6):
+        p = Problem(w)
+        prev = p.alpha.copy()
+        for (t, dT) in w.loads[::3]:
+            r = am.load_step(p, t, dT, omega=omega, tol=1e-7, record_energy=True)
+            e = np.array(r["energies"][1:])
+            assert np.all(np.diff(e) <= 1e-12 * np.abs(e).max())
+            assert np.all(p.alpha >= prev) and np.all(p.alpha <= 1.0)
+            prev = p.alpha.copy()
+        assert p.alpha[~(p.alpha_prev == 1)].max() > 0.5  # the crack has grown
+
+
+def test_oram_and_am_reach_same_stationary_point():
+    """On a step with a unique nearby stationary point, AM and ORAM(omega=1.5) agree."""
+    w = W.notched_square(n=16, n_steps=10, t_max=1.0)
+    res = []
+    for omega in (1.0, 1.5):
+        p = Problem(w)
+        for (t, dT) in w.loads[:6]:
+            am.load_step(p, t, dT, omega=omega, tol=1e-11)
+        res.append((p.u.copy(), p.alpha.copy()))
+    np.testing.assert_allclose(res[0][1], res[1][1], atol=1e-7)
+    np.testing.assert_allclose(res[0][0], res[1][0], atol=1e-7 * np.abs(res[0][0]).max())
+
+
+def test_oramn_matches_oram_and_converges_fast():
+    w = W.notched_square(n=16, n_steps=10, t_max=1.0)
+    p1, p2 = Problem(w), Problem(w)
+    for (t, dT) in w.loads[:6]:
+        am.load_step(p1, t, dT, omega=1.5, tol=1e-11)
+        r = am.load_step_oramn(p2, t, dT, omega=1.5, switch_tol=1e-2, rtol=1e-10)
+        assert r["status"] == "converged"
+    np.testing.assert_allclose(p1.alpha, p2.alpha, atol=1e-7)
+    np.testing.assert_allclose(p1.u, p2.u, atol=1e-7 * np.abs(p1.u).max())
+
+
+def test_thermal_no_damage_below_critical_jump():
+    """Thermal shock (Section 4.3): purely elastic for dT below dT_c (plane-strain reading);
+    above it damage appears first along the exposed face y = 0."""
+    w = W.thermal_shock(nx=32, ny=8)
+    dtc = W.thermal_critical_jump(w.E, w.nu, w.Gc, w.ell, w.beta)
+    p = Problem(w)
+    am.load_step(p, 0.0, 0.95 * dtc, omega=1.0, tol=1e-9)
+    assert p.alpha.max() == 0.0
+    am.load_step(p, 0.0, 1.05 * dtc, omega=1.0, tol=1e-9)
+    assert p.alpha.max() > 0
+    ybot = p.mesh.Y2 == 0
+    # an x-homogeneous band along the exposed face (small end effects of the side conditions)
+    assert p.alpha[ybot].min() > 0 and p.alpha[ybot].min() >= p.alpha[~ybot].max() - 1e-12
+    assert np.ptp(p.alpha[ybot]) < 0.5 * p.alpha[ybot].max()
