@@ -1,0 +1,248 @@
+/*
+ * pf.h -- C ABI of the GB300 phase-field fracture solver library (libpf.so).
+ *
+ * The library solves, one quasi-static load step at a time, the regularized fracture problem of
+ * Farrell & Maurini, "Linear and nonlinear solvers for variational phase-field models of brittle
+ * fracture": find a stationary point of
+ *
+ *   E(u, a) = int 1/2 a(a) A0 eps_eff(u):eps_eff(u) + Gc/c_w (w(a)/ell + ell |grad a|^2)
+ *
+ * (Section 1.1, eq. regenergy; thermal eigenstrain of eq. energytshock) over u in C_ubar and
+ * alpha in D_alpha_prev = { alpha_prev <= alpha <= 1 } (Section 1.1), with P1 triangles on a
+ * structured rectangle (Section 1.2, finite-element discretization).  Nonlinear solvers:
+ * alternate minimization (Algorithm 1), its over-relaxation ORAM (Algorithm 2) and ORAM composed
+ * with active-set Newton (Algorithm 3, Algorithm 4).  The linear subproblems (Section 3) are
+ * solved matrix-free by preconditioned CG with a geometric multigrid V-cycle.
+ *
+ * Conventions for every function:
+ *  - returns pf_status; never throws or aborts across the ABI.  On failure pf_last_error()
+ *    returns a thread-local message describing the last error of the calling thread.
+ *  - "device pointer" arguments are CUDA global-memory addresses on the sim's device; "host
+ *    pointer" arguments are ordinary CPU memory.  The caller owns every buffer it passes.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = legacy default stream).
+ *  - node order: the (nx+1)(ny+1) vertex grid row-major (x fastest), then, for crossed meshes,
+ *    the nx*ny cell-centre grid row-major.  u is interleaved (u_x, u_y) per node.
+ *  - doubled grid units: vertex (i, j) sits at (2i, 2j), the centre of cell (i, j) at
+ *    (2i+1, 2j+1); pins and damage boxes are given in these integer units.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pf_status {
+  PF_OK = 0,
+  PF_EINVAL = 1,    /* invalid argument or unsupported configuration */
+  PF_ENOMEM = 2,    /* workspace too small */
+  PF_ENOTCONV = 3,  /* iteration cap reached; the last iterate is kept and stays valid */
+  PF_ENUMERIC = 4,  /* NaN/Inf or breakdown detected in a reduction */
+  PF_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  PF_ECUDA = 6,     /* a CUDA runtime call failed */
+  PF_EBUSY = 7      /* the sim is in use by another call */
+} pf_status;
+
+enum { PF_MESH_RIGHT = 0, PF_MESH_CROSSED = 1 };
+enum { PF_AT1 = 1, PF_AT2 = 2 };
+enum { PF_PLANE_STRAIN = 0, PF_PLANE_STRESS = 1 };
+enum { PF_FP64 = 0, PF_MIXED = 1 };
+enum { PF_ALGO_AM = 0, PF_ALGO_ORAM = 1, PF_ALGO_ORAM_N = 2 };
+enum { PF_EDGE_LEFT = 0, PF_EDGE_RIGHT = 1, PF_EDGE_BOTTOM = 2, PF_EDGE_TOP = 3 };
+enum { PF_COMP_UX = 0, PF_COMP_UY = 1, PF_COMP_ALPHA = 2 };
+
+#define PF_MAX_PINS 8
+#define PF_MAX_BOXES 8
+
+/* Structured triangulation of [x0, x0+lx] x [y0, y0+ly] with nx x ny cells.
+ * kind = PF_MESH_RIGHT: each cell cut by its lower-left -> upper-right diagonal;
+ * kind = PF_MESH_CROSSED: each cell cut by both diagonals (extra centre node).
+ * Dirichlet data (the set C_ubar and the damage data of D_alpha, Section 1.1):
+ *   fixed[edge][comp] != 0 prescribes the component on that edge; the value is t*load for
+ *   displacement components (t = load amplitude of the step) and load for the damage.  Two
+ *   edges meeting at a corner must agree on a component they both prescribe.
+ *   pins: single prescribed nodes (doubled units), same value rule.
+ * boxes: nodes with box[k][0] <= X2 <= box[k][1] and box[k][2] <= Y2 <= box[k][3] start with
+ *   alpha = alpha_prev = box_value[k] (a pre-existing crack when 1). */
+typedef struct pf_mesh_desc {
+  int32_t kind, nx, ny;
+  double x0, y0, lx, ly;
+  uint8_t fixed[4][3];
+  double load[4][3];
+  int32_t n_pins;
+  int32_t pin_x2[PF_MAX_PINS], pin_y2[PF_MAX_PINS], pin_comp[PF_MAX_PINS];
+  double pin_load[PF_MAX_PINS];
+  int32_t n_boxes;
+  int32_t box[PF_MAX_BOXES][4];
+  double box_value[PF_MAX_BOXES];
+} pf_mesh_desc;
+
+/* Material (Section 1.1 and Section 4): Young's modulus E, Poisson ratio nu, toughness Gc,
+ * internal length ell, residual stiffness k_ell in a(alpha) = (1-alpha)^2 + k_ell, damage model
+ * (PF_AT1: w = alpha, PF_AT2: w = alpha^2), plane strain/stress, thermal expansion beta and the
+ * penetration length pen = 2 sqrt(kappa t) of T = -dT erfc(x2 / pen) (eq. tempfielderfc; x2
+ * measured from the bottom edge y = y0, T evaluated at element centroids). */
+typedef struct pf_material {
+  double E, nu, Gc, ell, k_ell;
+  int32_t model, plane;
+  double beta, pen;
+} pf_material;
+
+/* One quasi-static load step: displacement amplitude t and thermal shock amplitude dT. */
+typedef struct pf_load {
+  double t, dT;
+} pf_load;
+
+/* Solver options.  Defaults from pf_default_opts().  Tolerances:
+ *   am_tol: stop ORAM when max|alpha^k - alpha^{k-1}| <= am_tol and
+ *           max|u^k - u^{k-1}| <= am_tol * max|u^k| (Section 1.2 stopping criterion, see design
+ *           notes for the second part).
+ *   u_rtol: u-subproblem FP64 residual <= u_rtol * (first residual of the load step).
+ *   inner_rtol: relative tolerance of each inner FP32 CG solve (PF_MIXED).
+ *   rs_rtol: damage subproblem ||Phi||_2 <= rs_rtol * ||g0||_2 (Algorithm 4 termination).
+ *   alpha_cg_rtol: relative tolerance of the reduced Newton solves inside Algorithm 4.
+ *   zeta: zero tolerance of the active set (eq. reducedis).
+ *   switch_tol: ORAM-N switches to Newton when ||Phi^k|| / ||Phi^0|| <= switch_tol (Alg. 3).
+ *   newton_rtol: ORAM-N stops when ||Phi|| <= newton_rtol * ||Phi|| at the start of the step. */
+typedef struct pf_solver_opts {
+  int32_t algo, precision;
+  double omega;
+  double am_tol;
+  int32_t am_maxit;
+  double u_rtol, inner_rtol;
+  int32_t cg_maxit;
+  double rs_rtol;
+  int32_t rs_maxit;
+  double alpha_cg_rtol, zeta;
+  int32_t mg_levels_max;   /* 0 = as many as the mesh allows; 1 = Jacobi-preconditioned CG */
+  int32_t mg_degree;       /* Chebyshev smoothing steps per pre/post smoothing */
+  double switch_tol, newton_rtol;
+  int32_t newton_maxit, minres_maxit;
+  double minres_rtol;
+  int32_t use_graphs;      /* reserved: 0 */
+} pf_solver_opts;
+
+/* Per-step report (all counts summed over the step). */
+typedef struct pf_step_report {
+  int32_t status, am_iters, rs_iters, newton_iters;
+  int64_t cg_iters_u, cg_iters_alpha, krylov_iters_newton, outer_refinements;
+  double dalpha_inf, du_rel, phi_norm, phi_start, omega_bar_min;
+  double energy[3]; /* elastic, surface, total */
+  double seconds;
+} pf_step_report;
+
+typedef struct pf_ctx pf_ctx;
+typedef struct pf_sim pf_sim;
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* pf_last_error(void);
+
+/* Library version string. */
+const char* pf_version(void);
+
+/* Fill *o with defaults (ORAM, omega = 1, FP64, am_tol 1e-6, ...). */
+pf_status pf_default_opts(pf_solver_opts* o);
+
+/* Create a context bound to CUDA device `device` (makes it current on this thread).  The
+ * context allocates a small pinned host buffer; no device memory. */
+pf_status pf_ctx_create(int device, pf_ctx** out);
+void pf_ctx_destroy(pf_ctx* ctx);
+
+/* Bytes of device workspace pf_create_mesh needs for this mesh (both precisions included; the
+ * precision argument is accepted for forward compatibility and may be either PF_FP64 or
+ * PF_MIXED).  Returns 0 if the descriptor is invalid. */
+size_t pf_workspace_bytes(const pf_mesh_desc* d, int precision);
+
+/* Build the mesh, its multigrid hierarchy and the initial state (u = 0; alpha = alpha_prev = 0
+ * except inside the damage boxes, Section 4 pre-existing cracks) inside the caller-owned device
+ * workspace `dev_workspace` (at least pf_workspace_bytes bytes, 256-byte aligned), which must
+ * outlive the sim.  PF_ENOMEM if ws_bytes is too small; PF_EINVAL for invalid descriptors. */
+pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* dev_workspace,
+                         size_t ws_bytes, pf_sim** out);
+
+/* Set the material (Section 4 constants).  PF_EINVAL if nu not in (-1, 0.5), ell <= 0,
+ * k_ell < 0, E <= 0 or Gc <= 0.  Must be called before the first load step. */
+pf_status pf_set_material(pf_sim* sim, const pf_material* m);
+
+/* Solve one load step (Algorithm 1/2/3 according to o->algo) on `stream`, in place on the
+ * resident state: alpha_prev <- alpha, Dirichlet data t*load written into u, then iterate to
+ * convergence.  Blocks the host until the step finishes (convergence decisions are read back).
+ * On PF_ENOTCONV the last iterate is kept and the state stays valid. rep may be NULL. */
+pf_status pf_load_step(pf_sim* sim, const pf_load* L, const pf_solver_opts* o, void* stream,
+                       pf_step_report* rep);
+
+/* Energies (elastic, surface, total) of the resident state for the last load (FP64,
+ * deterministic reduction).  Synchronous. */
+pf_status pf_energy(pf_sim* sim, void* stream, double out[3]);
+
+/* One load step for each of n sims (loads[i] for sims[i]) with shared options; per-sim reports
+ * in reps[i] (may be NULL).  The sims' work is issued concurrently; returns the worst status. */
+pf_status pf_solve_batch(pf_ctx* ctx, pf_sim* const* sims, const pf_load* loads, int n,
+                         const pf_solver_opts* o, void* stream, pf_step_report* reps);
+
+/* Copy the resident state to / from host memory (FP64, node order above, u interleaved).  Any
+ * pointer may be NULL to skip that field.  Synchronous.  pf_set_fields also sets the current
+ * load used by the operator entry points below. */
+pf_status pf_get_fields(pf_sim* sim, double* u, double* alpha, double* alpha_prev);
+pf_status pf_set_fields(pf_sim* sim, const double* u, const double* alpha,
+                        const double* alpha_prev);
+
+/* Mesh sizes: nodes, elements and multigrid levels. */
+pf_status pf_sim_info(const pf_sim* sim, int64_t* n_nodes, int64_t* n_elements, int32_t* levels);
+
+void pf_destroy(pf_sim* sim);
+
+/* ---------------------------------------------------------------------------------------------
+ * Operator entry points (single kernels or single subproblem solves on the resident state).
+ * They exist so that each step of the method can be checked on its own.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Set the current load (t, dT) and write the Dirichlet data t*load into u (the lift applied at
+ * the start of every load step) without solving; alpha_prev is not touched. */
+pf_status pf_set_load(pf_sim* sim, const pf_load* L);
+
+/* y = K(alpha) x for the elasticity operator E_uu (Section 1.2, eq. elasticity) with the
+ * resident alpha.  x, y: device pointers to 2*n_nodes values, double when precision ==
+ * PF_FP64, float when PF_MIXED (then alpha is read from its FP32 copy).  masked != 0 applies
+ * the operator of the free dofs: x is read as 0 on prescribed dofs and y = x there. */
+pf_status pf_op_elastic_apply(pf_sim* sim, int precision, int masked, const void* x, void* y,
+                              void* stream);
+
+/* r = -(E_u) = f - K(alpha) u on free dofs, 0 on prescribed dofs, for the resident u, alpha and
+ * the current load (thermal load vector included).  r: device, 2*n_nodes doubles.
+ * *norm2 (host) receives ||r||^2. */
+pf_status pf_op_elastic_residual(pf_sim* sim, double* r, double* norm2, void* stream);
+
+/* Damage gradient E_alpha = H alpha + g0 at the resident u, alpha (Section 1.2 and eq.
+ * helmholtz), its MCP Fischer-Burmeister residual Phi on the box [lower, upper] (Section 2.4)
+ * and the active-set flags (eq. reducedis; 1 = active).  F, Phi: device, n_nodes doubles;
+ * active: device, n_nodes bytes (may be NULL).  *phi_norm2 (host) receives ||Phi||^2. */
+pf_status pf_op_damage_gradient(pf_sim* sim, double* F, double* Phi, uint8_t* active,
+                                double* phi_norm2, void* stream);
+
+/* y = H(q(u)) x, the damage Hessian E_aa at the resident u (precision as above; n_nodes
+ * values). */
+pf_status pf_op_damage_apply(pf_sim* sim, int precision, const void* x, void* y, void* stream);
+
+/* Solve the u-subproblem of Algorithm 1 at the resident alpha and current load, in place
+ * (u <- minimizer; Section 3.1 solver: PCG + multigrid).  rep may be NULL. */
+pf_status pf_op_u_solve(pf_sim* sim, const pf_solver_opts* o, void* stream, pf_step_report* rep);
+
+/* Solve the alpha-subproblem of Algorithm 1 (box-constrained, Algorithm 4 with PCG + multigrid
+ * on the inactive set, Section 3.2) at the resident u, in place, with bounds
+ * [alpha_prev, 1] and the damage Dirichlet data.  rep may be NULL. */
+pf_status pf_op_alpha_solve(pf_sim* sim, const pf_solver_opts* o, void* stream,
+                            pf_step_report* rep);
+
+/* ||Phi||_2 of the full optimality system (eq. kkt: E_u on free dofs, MCP residual of
+ * E_alpha) at the resident state and current load.  Synchronous. */
+pf_status pf_op_full_residual(pf_sim* sim, double* phi_norm, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H */

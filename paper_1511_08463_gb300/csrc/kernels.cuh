@@ -1,0 +1,99 @@
+// Host-side launchers of the libpf kernels (definitions in ops_*.cu and kernels_misc.cu).
+#pragma once
+#include "stencil.cuh"
+
+namespace pf {
+
+// ---- stencil operators (ops_elastic.cu, ops_damage.cu) ----------------------------------------
+template <class T>
+void launch_elastic(cudaStream_t s, const Grid& g, const Mat& m, int coef, int mode, bool eigen,
+                    bool dot, const ElasticArgs<T>& a);
+template <class T>
+void launch_damage(cudaStream_t s, const Grid& g, const Mat& m, int mode, bool dot,
+                   const DamageArgs<T>& a);
+
+// ---- pointwise vector kernels (kernels_misc.cu) -----------------------------------------------
+template <class T>
+void vec_fill(cudaStream_t s, T* y, T v, size_t n);
+template <class TO, class TI>
+void vec_convert(cudaStream_t s, TO* y, const TI* x, size_t n);
+void vec_add_f32_to_f64(cudaStream_t s, double* x, const float* d, size_t n);
+template <class T>
+void vec_add(cudaStream_t s, T* x, const T* d, size_t n);  // x += d
+template <class T>
+void vec_mul(cudaStream_t s, T* z, const T* a, const T* b, size_t n);  // z = a .* b
+template <class T>
+void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot);
+// CG: a = *rz / *pAp; x += a p; r -= a Ap; out = r.r
+template <class T>
+void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n,
+                  const double* rz, const double* pAp, RedSlot slot);
+// CG: p = z + (*rz_new / *rz_old) p   (rz_old == nullptr: p = z)
+template <class T>
+void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
+                 const double* rz_old);
+
+// u <- u + omega (xt - u); reductions: max |du|, max |u_new|
+void relax_u(cudaStream_t s, double* u, const double* xt, double omega, size_t n2, RedSlot slot);
+// max feasible step along alpha + w (at - alpha) in [lo, hi]: out = -min ratio (MAX reduction)
+void omega_star(cudaStream_t s, const Grid& g, const double* alpha, const double* at,
+                const double* lo, RedSlot slot);
+// alpha <- clip(alpha + w (at - alpha)); alpha32 = float(alpha); out = max |dalpha|
+void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at, const double* lo,
+                 double w, float* alpha32, RedSlot slot);
+// u[fixed dofs] = t * load
+struct LiftData {
+  double load[4][3];
+  double pin_load[PF_MAX_PINS];
+};
+void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld);
+// u <- u on free dofs, masked copy helpers
+template <class T>
+void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp);  // zero prescribed components
+
+// ---- element-wise kernels -----------------------------------------------------------------------
+template <class T>
+void elastic_coef(cudaStream_t s, const Grid& g, const Mat& m, const T* alpha, T* coef);
+// q_T = A0 eps_eff : eps_eff (FP64); w64 = q + c2, w32 = float(q + c2)
+void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
+              double* q, double* w64, float* w32);
+// energies: out[0] elastic, out[1] surface
+void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* alpha,
+            const double* eig, RedSlot slot);
+// coarse element coefficient = mean of its four children
+template <class T>
+void coarsen_coef(cudaStream_t s, const Grid& gf, const Grid& gc, const T* cf, T* cc);
+// inverse l1 diagonal: elastic (2 per node) or damage (1 per node)
+template <class T>
+void l1_dinv_elastic(cudaStream_t s, const Grid& g, const Mat& m, const T* coef, T* dinv);
+template <class T>
+void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* dinv);
+
+// ---- multigrid transfer -------------------------------------------------------------------------
+// bc = P^T rf on the coarse grid (comp_base: 0 elastic (2 comps), 2 damage (1 comp)); coarse
+// prescribed components set to 0.
+template <class T>
+void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
+                  const T* rf, T* bc);
+// xf += P xc on free components; excl (fine, may be null) zeroes excluded nodes
+template <class T>
+void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
+                 const T* xc, T* xf, const uint8_t* excl);
+
+// ---- coarsest level dense solve -----------------------------------------------------------------
+template <class T>
+void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef,
+                     T* A, T* diag0);
+template <class T>
+void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0);
+template <class T>
+void coarse_solve(cudaStream_t s, int n, const T* L, const T* b, T* x);
+
+// ---- misc for the damage solve ------------------------------------------------------------------
+// steepest-descent fallback of Algorithm 4: v = -pb qb Phi, dg = (pa - pb qa) Phi
+void merit_parts(cudaStream_t s, const Grid& g, const double* x, const double* F,
+                 const double* lo, double* v, double* dg);
+// d = -(dg + Hv)
+void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d);
+
+}  // namespace pf

@@ -1,0 +1,758 @@
+// Pointwise, element-wise, transfer and coarse-solve kernels of libpf.
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace pf {
+
+static inline unsigned nblocks(size_t n, int bs = RED_THREADS) {
+  size_t b = (n + bs - 1) / bs;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+// reduction kernels use a grid-stride loop over at most MAX_RED_BLOCKS blocks
+static inline unsigned rblocks(size_t n) {
+  size_t b = (n + RED_THREADS - 1) / RED_THREADS;
+  if (b > MAX_RED_BLOCKS) b = MAX_RED_BLOCKS;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------------------------------------
+// pointwise vectors
+// ---------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_fill(T* y, T v, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+template <class T>
+void vec_fill(cudaStream_t s, T* y, T v, size_t n) {
+  k_fill<<<nblocks(n), RED_THREADS, 0, s>>>(y, v, n);
+}
+template void vec_fill<double>(cudaStream_t, double*, double, size_t);
+template void vec_fill<float>(cudaStream_t, float*, float, size_t);
+
+template <class TO, class TI>
+__global__ void k_convert(TO* y, const TI* x, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = TO(x[i]);
+}
+template <class TO, class TI>
+void vec_convert(cudaStream_t s, TO* y, const TI* x, size_t n) {
+  k_convert<TO, TI><<<nblocks(n), RED_THREADS, 0, s>>>(y, x, n);
+}
+template void vec_convert<float, double>(cudaStream_t, float*, const double*, size_t);
+template void vec_convert<double, float>(cudaStream_t, double*, const float*, size_t);
+template void vec_convert<double, double>(cudaStream_t, double*, const double*, size_t);
+
+__global__ void k_add_f32_to_f64(double* x, const float* d, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += (double)d[i];
+}
+void vec_add_f32_to_f64(cudaStream_t s, double* x, const float* d, size_t n) {
+  k_add_f32_to_f64<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n);
+}
+
+template <class T>
+__global__ void k_add(T* x, const T* d, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
+}
+template <class T>
+void vec_add(cudaStream_t s, T* x, const T* d, size_t n) {
+  k_add<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n);
+}
+template void vec_add<double>(cudaStream_t, double*, const double*, size_t);
+template void vec_add<float>(cudaStream_t, float*, const float*, size_t);
+
+template <class T>
+__global__ void k_mul(T* z, const T* a, const T* b, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a[i] * b[i];
+}
+template <class T>
+void vec_mul(cudaStream_t s, T* z, const T* a, const T* b, size_t n) {
+  k_mul<<<nblocks(n), RED_THREADS, 0, s>>>(z, a, b, n);
+}
+template void vec_mul<double>(cudaStream_t, double*, const double*, const double*, size_t);
+template void vec_mul<float>(cudaStream_t, float*, const float*, const float*, size_t);
+
+template <class T>
+__global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
+  double v[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    v[0] += double(x[i]) * double(y[i]);
+  block_reduce_finalize<1, false>(v, slot);
+}
+template <class T>
+void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot) {
+  k_dot<<<rblocks(n), RED_THREADS, 0, s>>>(x, y, n, slot);
+}
+template void vec_dot<double>(cudaStream_t, const double*, const double*, size_t, RedSlot);
+template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, RedSlot);
+
+template <class T>
+__global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
+                        const double* pAp, RedSlot slot) {
+  const double a = *rz / *pAp;
+  const T at = T(a);
+  double v[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    x[i] += at * p[i];
+    T ri = r[i] - at * Ap[i];
+    r[i] = ri;
+    v[0] += double(ri) * double(ri);
+  }
+  block_reduce_finalize<1, false>(v, slot);
+}
+template <class T>
+void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
+                  const double* pAp, RedSlot slot) {
+  k_cg_xr<<<rblocks(n), RED_THREADS, 0, s>>>(x, r, p, Ap, n, rz, pAp, slot);
+}
+template void cg_update_xr<double>(cudaStream_t, double*, double*, const double*, const double*,
+                                   size_t, const double*, const double*, RedSlot);
+template void cg_update_xr<float>(cudaStream_t, float*, float*, const float*, const float*, size_t,
+                                  const double*, const double*, RedSlot);
+
+template <class T>
+__global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const double* rz_old) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (rz_old == nullptr) {
+    p[i] = z[i];
+  } else {
+    const T b = T(*rz_new / *rz_old);
+    p[i] = z[i] + b * p[i];
+  }
+}
+template <class T>
+void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
+                 const double* rz_old) {
+  k_cg_p<<<nblocks(n), RED_THREADS, 0, s>>>(p, z, n, rz_new, rz_old);
+}
+template void cg_update_p<double>(cudaStream_t, double*, const double*, size_t, const double*,
+                                  const double*);
+template void cg_update_p<float>(cudaStream_t, float*, const float*, size_t, const double*,
+                                 const double*);
+
+// over-relaxation of u (Algorithm 2): prescribed dofs have xt == u, so they do not move
+__global__ void k_relax_u(double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
+  double v[2] = {0.0, 0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double uo = u[i];
+    double un = uo + omega * (xt[i] - uo);
+    u[i] = un;
+    v[0] = fmax(v[0], fabs(un - uo));
+    v[1] = fmax(v[1], fabs(un));
+  }
+  block_reduce_finalize<2, true>(v, slot);
+}
+void relax_u(cudaStream_t s, double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
+  k_relax_u<<<rblocks(n2), RED_THREADS, 0, s>>>(u, xt, omega, n2, slot);
+}
+
+__device__ __forceinline__ double upper_of(const Grid& g, int node, double lo) {
+  int X2, Y2;
+  node_coords(g, node, X2, Y2);
+  return is_fixed(g, X2, Y2, 2) ? lo : 1.0;
+}
+
+// largest w with lo <= alpha + w (at - alpha) <= hi at every node: out[0] = -w*
+__global__ void k_omega_star(Grid g, const double* alpha, const double* at, const double* lo,
+                             RedSlot slot) {
+  double v[1] = {-INFINITY};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    double a = alpha[i], d = at[i] - a;
+    double l = lo[i], h = upper_of(g, i, l);
+    double r = INFINITY;
+    if (d > 0.0) r = (h - a) / d;
+    else if (d < 0.0) r = (l - a) / d;
+    v[0] = fmax(v[0], -r);
+  }
+  block_reduce_finalize<1, true>(v, slot);
+}
+void omega_star(cudaStream_t s, const Grid& g, const double* alpha, const double* at,
+                const double* lo, RedSlot slot) {
+  k_omega_star<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, slot);
+}
+
+__global__ void k_relax_alpha(Grid g, double* alpha, const double* at, const double* lo, double w,
+                              float* alpha32, RedSlot slot) {
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    double a = alpha[i];
+    double l = lo[i], h = upper_of(g, i, l);
+    double an = fmin(fmax(a + w * (at[i] - a), l), h);
+    alpha[i] = an;
+    if (alpha32) alpha32[i] = (float)an;
+    v[0] = fmax(v[0], fabs(an - a));
+  }
+  block_reduce_finalize<1, true>(v, slot);
+}
+void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at, const double* lo,
+                 double w, float* alpha32, RedSlot slot) {
+  k_relax_alpha<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, w, alpha32, slot);
+}
+
+__global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nv) return;  // only vertices lie on edges; pins checked below for all nodes
+  int X2, Y2;
+  node_coords(g, node, X2, Y2);
+  for (int c = 0; c < 2; ++c) {
+    if (X2 == 0 && g.fixed[0][c]) u[2 * node + c] = t * ld.load[0][c];
+    if (X2 == 2 * g.nx && g.fixed[1][c]) u[2 * node + c] = t * ld.load[1][c];
+    if (Y2 == 0 && g.fixed[2][c]) u[2 * node + c] = t * ld.load[2][c];
+    if (Y2 == 2 * g.ny && g.fixed[3][c]) u[2 * node + c] = t * ld.load[3][c];
+  }
+}
+__global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
+  for (int k = 0; k < g.npins; ++k) {
+    if (g.pin_comp[k] > 1) continue;
+    int X2 = g.pin_x2[k], Y2 = g.pin_y2[k], node;
+    if ((X2 & 1) == 0) node = (Y2 / 2) * (g.nx + 1) + X2 / 2;
+    else node = g.nv + (Y2 / 2) * g.nx + X2 / 2;
+    u[2 * node + g.pin_comp[k]] = t * ld.pin_load[k];
+  }
+}
+void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld) {
+  k_lift<<<nblocks(g.nv), RED_THREADS, 0, s>>>(g, u, t, ld);
+  if (g.npins > 0) k_lift_pins<<<1, 1, 0, s>>>(g, u, t, ld);
+}
+
+template <class T>
+__global__ void k_mask_fixed(Grid g, T* v, int ncomp) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n) return;
+  int X2, Y2;
+  node_coords(g, node, X2, Y2);
+  if (ncomp == 2) {
+    if (is_fixed(g, X2, Y2, 0)) v[2 * node] = T(0);
+    if (is_fixed(g, X2, Y2, 1)) v[2 * node + 1] = T(0);
+  } else {
+    if (is_fixed(g, X2, Y2, 2)) v[node] = T(0);
+  }
+}
+template <class T>
+void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp) {
+  k_mask_fixed<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, v, ncomp);
+}
+template void mask_fixed<double>(cudaStream_t, const Grid&, double*, int);
+template void mask_fixed<float>(cudaStream_t, const Grid&, float*, int);
+
+// ---------------------------------------------------------------------------------------------
+// element-wise kernels: one thread per cell
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cell_nodes(const Grid& g, int ci, int cj, int t, int& n0, int& n1,
+                                           int& n2) {
+  int v00 = cj * (g.nx + 1) + ci, v10 = v00 + 1, v01 = v00 + g.nx + 1, v11 = v01 + 1;
+  if (g.kind == CROSSED) {
+    int c = g.nv + cj * g.nx + ci;
+    if (t == 0) { n0 = v00; n1 = v10; n2 = c; }
+    else if (t == 1) { n0 = v10; n1 = v11; n2 = c; }
+    else if (t == 2) { n0 = v11; n1 = v01; n2 = c; }
+    else { n0 = v01; n1 = v00; n2 = c; }
+  } else {
+    if (t == 0) { n0 = v00; n1 = v10; n2 = v11; }
+    else { n0 = v00; n1 = v11; n2 = v01; }
+  }
+}
+
+__device__ __forceinline__ int gxr(int kind, int t, int k) { return gx(kind, t, k); }
+__device__ __forceinline__ int gyr(int kind, int t, int k) { return gy(kind, t, k); }
+
+template <class T>
+__global__ void k_elastic_coef(Grid g, Mat m, const T* alpha, T* coef) {
+  int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncell) return;
+  int cj = cell / g.nx, ci = cell - cj * g.nx;
+  int NE = elems_per_cell(g.kind);
+  for (int t = 0; t < NE; ++t) {
+    int n0, n1, n2;
+    cell_nodes(g, ci, cj, t, n0, n1, n2);
+    coef[cell * NE + t] = abar3<T>(alpha[n0], alpha[n1], alpha[n2], T(m.k_ell));
+  }
+}
+template <class T>
+void elastic_coef(cudaStream_t s, const Grid& g, const Mat& m, const T* alpha, T* coef) {
+  k_elastic_coef<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, alpha, coef);
+}
+template void elastic_coef<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
+template void elastic_coef<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
+
+__device__ __forceinline__ void strain_of(const Grid& g, int t, const double* u, int n0, int n1,
+                                          int n2, double& exx, double& eyy, double& gxy) {
+  int nn[3] = {n0, n1, n2};
+  double sx = 0, sy = 0, s1 = 0, s2 = 0;
+  for (int k = 0; k < 3; ++k) {
+    double ux = u[2 * nn[k]], uy = u[2 * nn[k] + 1];
+    int cx = gxr(g.kind, t, k), cy = gyr(g.kind, t, k);
+    sx += cx * ux;
+    sy += cy * uy;
+    s1 += cy * ux;
+    s2 += cx * uy;
+  }
+  exx = g.ihx * sx;
+  eyy = g.ihy * sy;
+  gxy = g.ihy * s1 + g.ihx * s2;
+}
+
+__global__ void k_damage_q(Grid g, Mat m, const double* u, const double* eig, double* q,
+                           double* w64, float* w32) {
+  int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncell) return;
+  int cj = cell / g.nx, ci = cell - cj * g.nx;
+  int NE = elems_per_cell(g.kind);
+  for (int t = 0; t < NE; ++t) {
+    int n0, n1, n2;
+    cell_nodes(g, ci, cj, t, n0, n1, n2);
+    double exx, eyy, gxy;
+    strain_of(g, t, u, n0, n1, n2, exx, eyy, gxy);
+    if (eig) {
+      double e0 = eig[cj * NE + t];
+      exx -= e0;
+      eyy -= e0;
+    }
+    double qq = m.lam2mu * (exx * exx + eyy * eyy) + 2.0 * m.lam * exx * eyy + m.mu * gxy * gxy;
+    q[cell * NE + t] = qq;
+    if (w64) w64[cell * NE + t] = qq + m.c2;
+    if (w32) w32[cell * NE + t] = (float)(qq + m.c2);
+  }
+}
+void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
+              double* q, double* w64, float* w32) {
+  k_damage_q<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, eig, q, w64, w32);
+}
+
+__global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, const double* eig,
+                         RedSlot slot) {
+  double v[2] = {0.0, 0.0};
+  int NE = elems_per_cell(g.kind);
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell;
+       cell += gridDim.x * blockDim.x) {
+    int cj = cell / g.nx, ci = cell - cj * g.nx;
+    for (int t = 0; t < NE; ++t) {
+      int n0, n1, n2;
+      cell_nodes(g, ci, cj, t, n0, n1, n2);
+      double exx, eyy, gxy;
+      strain_of(g, t, u, n0, n1, n2, exx, eyy, gxy);
+      if (eig) {
+        double e0 = eig[cj * NE + t];
+        exx -= e0;
+        eyy -= e0;
+      }
+      double qq = m.lam2mu * (exx * exx + eyy * eyy) + 2.0 * m.lam * exx * eyy + m.mu * gxy * gxy;
+      double a0 = alpha[n0], a1 = alpha[n1], a2 = alpha[n2];
+      double ab = abar3<double>(a0, a1, a2, m.k_ell);
+      v[0] += 0.5 * ab * qq * g.area;
+      double wbar;
+      if (m.model == PF_AT1) wbar = (a0 + a1 + a2) * (1.0 / 3.0);
+      else wbar = (a0 * a0 + a1 * a1 + a2 * a2 + a0 * a1 + a1 * a2 + a2 * a0) * (1.0 / 6.0);
+      double gax = g.ihx * (gxr(g.kind, t, 0) * a0 + gxr(g.kind, t, 1) * a1 + gxr(g.kind, t, 2) * a2);
+      double gay = g.ihy * (gyr(g.kind, t, 0) * a0 + gyr(g.kind, t, 1) * a1 + gyr(g.kind, t, 2) * a2);
+      v[1] += m.gc_cw * (wbar / m.ell + m.ell * (gax * gax + gay * gay)) * g.area;
+    }
+  }
+  block_reduce_finalize<2, false>(v, slot);
+}
+void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* alpha,
+            const double* eig, RedSlot slot) {
+  k_energy<<<rblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, alpha, eig, slot);
+}
+
+// children of coarse element t of coarse cell (I, J): fine cells and fine element types
+//  RIGHT   t0 (lower): (2I,2J).0, (2I+1,2J).0, (2I+1,2J).1, (2I+1,2J+1).0
+//          t1 (upper): (2I,2J).1, (2I,2J+1).0, (2I,2J+1).1, (2I+1,2J+1).1
+//  CROSSED t0 (bottom): BL.0, BL.1, BR.0, BR.3     t1 (right): BR.1, BR.2, TR.1, TR.0
+//          t2 (top):    TR.2, TR.3, TL.2, TL.1     t3 (left):  TL.3, TL.0, BL.3, BL.2
+template <class T>
+__global__ void k_coarsen(Grid gf, Grid gc, const T* cf, T* cc) {
+  int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= gc.ncell) return;
+  int J = cell / gc.nx, I = cell - J * gc.nx;
+  int NE = elems_per_cell(gc.kind);
+  auto F = [&](int di, int dj, int t) -> T {
+    return cf[((2 * J + dj) * gf.nx + (2 * I + di)) * NE + t];
+  };
+  if (gc.kind == RIGHT) {
+    cc[cell * 2 + 0] = (F(0, 0, 0) + F(1, 0, 0) + F(1, 0, 1) + F(1, 1, 0)) * T(0.25);
+    cc[cell * 2 + 1] = (F(0, 0, 1) + F(0, 1, 0) + F(0, 1, 1) + F(1, 1, 1)) * T(0.25);
+  } else {
+    cc[cell * 4 + 0] = (F(0, 0, 0) + F(0, 0, 1) + F(1, 0, 0) + F(1, 0, 3)) * T(0.25);
+    cc[cell * 4 + 1] = (F(1, 0, 1) + F(1, 0, 2) + F(1, 1, 1) + F(1, 1, 0)) * T(0.25);
+    cc[cell * 4 + 2] = (F(1, 1, 2) + F(1, 1, 3) + F(0, 1, 2) + F(0, 1, 1)) * T(0.25);
+    cc[cell * 4 + 3] = (F(0, 1, 3) + F(0, 1, 0) + F(0, 0, 3) + F(0, 0, 2)) * T(0.25);
+  }
+}
+template <class T>
+void coarsen_coef(cudaStream_t s, const Grid& gf, const Grid& gc, const T* cf, T* cc) {
+  k_coarsen<<<nblocks(gc.ncell), RED_THREADS, 0, s>>>(gf, gc, cf, cc);
+}
+template void coarsen_coef<double>(cudaStream_t, const Grid&, const Grid&, const double*, double*);
+template void coarsen_coef<float>(cudaStream_t, const Grid&, const Grid&, const float*, float*);
+
+// element (cell offset, element type, local index) lists around a node
+__device__ __forceinline__ int node_elements(const Grid& g, int node, int* cells, int* ts,
+                                             int* ks) {
+  int cnt = 0;
+  auto push = [&](int ci, int cj, int t, int k) {
+    if (ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny) {
+      cells[cnt] = cj * g.nx + ci;
+      ts[cnt] = t;
+      ks[cnt] = k;
+      ++cnt;
+    }
+  };
+  if (node < g.nv) {
+    int j = node / (g.nx + 1), i = node - j * (g.nx + 1);
+    if (g.kind == CROSSED) {
+      push(i, j, 0, 0); push(i, j, 3, 1);
+      push(i - 1, j, 0, 1); push(i - 1, j, 1, 0);
+      push(i - 1, j - 1, 1, 1); push(i - 1, j - 1, 2, 0);
+      push(i, j - 1, 2, 1); push(i, j - 1, 3, 0);
+    } else {
+      push(i, j, 0, 0); push(i, j, 1, 0);
+      push(i - 1, j, 0, 1);
+      push(i - 1, j - 1, 0, 2); push(i - 1, j - 1, 1, 1);
+      push(i, j - 1, 1, 2);
+    }
+  } else {
+    int c = node - g.nv, j = c / g.nx, i = c - j * g.nx;
+    for (int t = 0; t < 4; ++t) push(i, j, t, 2);
+  }
+  return cnt;
+}
+
+// l1 row sums of the assembled element matrices: D_ii = sum_T sum_j |K_T(i, j)|, so that the
+// spectrum of D^{-1} K lies in (0, 1].
+template <class T>
+__global__ void k_l1_elastic(Grid g, Mat m, const T* coef, T* dinv) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n) return;
+  int cells[8], ts[8], ks[8];
+  int cnt = node_elements(g, node, cells, ts, ks);
+  int NE = elems_per_cell(g.kind);
+  double dx = 0.0, dy = 0.0;
+  for (int e = 0; e < cnt; ++e) {
+    int t = ts[e], k = ks[e];
+    double w = double(coef[cells[e] * NE + t]) * g.area;
+    double gkx = gxr(g.kind, t, k) * g.ihx, gky = gyr(g.kind, t, k) * g.ihy;
+    double sx = 0.0, sy = 0.0;
+    for (int l = 0; l < 3; ++l) {
+      double glx = gxr(g.kind, t, l) * g.ihx, gly = gyr(g.kind, t, l) * g.ihy;
+      sx += fabs(gkx * glx * m.lam2mu + gky * gly * m.mu) + fabs(gkx * gly * m.lam + gky * glx * m.mu);
+      sy += fabs(gky * glx * m.lam + gkx * gly * m.mu) + fabs(gky * gly * m.lam2mu + gkx * glx * m.mu);
+    }
+    dx += w * sx;
+    dy += w * sy;
+  }
+  int X2, Y2;
+  node_coords(g, node, X2, Y2);
+  dinv[2 * node] = (is_fixed(g, X2, Y2, 0) || dx <= 0.0) ? T(0) : T(1.0 / dx);
+  dinv[2 * node + 1] = (is_fixed(g, X2, Y2, 1) || dy <= 0.0) ? T(0) : T(1.0 / dy);
+}
+template <class T>
+void l1_dinv_elastic(cudaStream_t s, const Grid& g, const Mat& m, const T* coef, T* dinv) {
+  k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, coef, dinv);
+}
+template void l1_dinv_elastic<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
+template void l1_dinv_elastic<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
+
+template <class T>
+__global__ void k_l1_damage(Grid g, Mat m, const T* w, T* dinv) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n) return;
+  int cells[8], ts[8], ks[8];
+  int cnt = node_elements(g, node, cells, ts, ks);
+  int NE = elems_per_cell(g.kind);
+  double dd = 0.0;
+  for (int e = 0; e < cnt; ++e) {
+    int t = ts[e], k = ks[e];
+    double me = double(w[cells[e] * NE + t]) * g.area / 12.0;
+    double gkx = gxr(g.kind, t, k) * g.ihx, gky = gyr(g.kind, t, k) * g.ihy;
+    for (int l = 0; l < 3; ++l) {
+      double glx = gxr(g.kind, t, l) * g.ihx, gly = gyr(g.kind, t, l) * g.ihy;
+      dd += fabs(me * (l == k ? 2.0 : 1.0) + m.c1 * g.area * (gkx * glx + gky * gly));
+    }
+  }
+  int X2, Y2;
+  node_coords(g, node, X2, Y2);
+  dinv[node] = (is_fixed(g, X2, Y2, 2) || dd <= 0.0) ? T(0) : T(1.0 / dd);
+}
+template <class T>
+void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* dinv) {
+  k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, w, dinv);
+}
+template void l1_dinv_damage<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
+template void l1_dinv_damage<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
+
+// ---------------------------------------------------------------------------------------------
+// multigrid transfer (P1 nodal interpolation between nested structured meshes)
+// ---------------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T fget(const Grid& gf, const T* v, bool centre, int i, int j, int c,
+                                  int ncomp) {
+  if (!centre) {
+    if (i < 0 || i > gf.nx || j < 0 || j > gf.ny) return T(0);
+    return v[(j * (gf.nx + 1) + i) * ncomp + c];
+  }
+  if (i < 0 || i >= gf.nx || j < 0 || j >= gf.ny) return T(0);
+  return v[(gf.nv + j * gf.nx + i) * ncomp + c];
+}
+
+template <class T>
+__global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* rf, T* bc) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gc.n) return;
+  int X2, Y2;
+  node_coords(gc, node, X2, Y2);
+  for (int c = 0; c < ncomp; ++c) {
+    T acc;
+    if ((X2 & 1) == 0) {  // coarse vertex (I, J) = fine vertex (2I, 2J)
+      int i = X2, j = Y2;  // fine vertex indices 2I, 2J
+      acc = fget(gf, rf, false, i, j, c, ncomp);
+      T h = fget(gf, rf, false, i - 1, j, c, ncomp) + fget(gf, rf, false, i + 1, j, c, ncomp) +
+            fget(gf, rf, false, i, j - 1, c, ncomp) + fget(gf, rf, false, i, j + 1, c, ncomp);
+      if (gf.kind == RIGHT) {
+        h += fget(gf, rf, false, i + 1, j + 1, c, ncomp) + fget(gf, rf, false, i - 1, j - 1, c, ncomp);
+      } else {
+        h += fget(gf, rf, true, i, j, c, ncomp) + fget(gf, rf, true, i - 1, j, c, ncomp) +
+             fget(gf, rf, true, i, j - 1, c, ncomp) + fget(gf, rf, true, i - 1, j - 1, c, ncomp);
+      }
+      acc += T(0.5) * h;
+    } else {  // coarse centre (I, J) = fine vertex (2I+1, 2J+1)
+      int I = X2 / 2, J = Y2 / 2;
+      acc = fget(gf, rf, false, 2 * I + 1, 2 * J + 1, c, ncomp);
+      T h = fget(gf, rf, true, 2 * I, 2 * J, c, ncomp) + fget(gf, rf, true, 2 * I + 1, 2 * J, c, ncomp) +
+            fget(gf, rf, true, 2 * I, 2 * J + 1, c, ncomp) +
+            fget(gf, rf, true, 2 * I + 1, 2 * J + 1, c, ncomp);
+      acc += T(0.5) * h;
+    }
+    if (is_fixed(gc, X2, Y2, comp_base + c)) acc = T(0);
+    bc[node * ncomp + c] = acc;
+  }
+}
+template <class T>
+void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
+                  const T* rf, T* bc) {
+  k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc);
+}
+template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
+                                   double*);
+template void restrict_res<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
+                                  float*);
+
+template <class T>
+__device__ __forceinline__ T cget(const Grid& gc, const T* v, bool centre, int I, int J, int c,
+                                  int ncomp) {
+  if (!centre) return v[(J * (gc.nx + 1) + I) * ncomp + c];
+  return v[(gc.nv + J * gc.nx + I) * ncomp + c];
+}
+
+template <class T>
+__global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* xc, T* xf,
+                          const uint8_t* excl) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gf.n) return;
+  int X2, Y2;
+  node_coords(gf, node, X2, Y2);
+  bool ex = excl && excl[node];
+  for (int c = 0; c < ncomp; ++c) {
+    T v;
+    if (node < gf.nv) {
+      int i = X2 / 2, j = Y2 / 2, I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
+      if (!pi && !pj) v = cget(gc, xc, false, I, J, c, ncomp);
+      else if (pi && !pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J, c, ncomp));
+      else if (!pi && pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I, J + 1, c, ncomp));
+      else if (gf.kind == RIGHT)
+        v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J + 1, c, ncomp));
+      else v = cget(gc, xc, true, I, J, c, ncomp);
+    } else {
+      int cc = node - gf.nv, j = cc / gf.nx, i = cc - j * gf.nx;
+      int I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
+      v = T(0.5) * (cget(gc, xc, false, I + pi, J + pj, c, ncomp) + cget(gc, xc, true, I, J, c, ncomp));
+    }
+    if (ex || is_fixed(gf, X2, Y2, comp_base + c)) v = T(0);
+    xf[node * ncomp + c] += v;
+  }
+}
+template <class T>
+void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
+                 const T* xc, T* xf, const uint8_t* excl) {
+  k_prolong<<<nblocks(gf.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, xc, xf, excl);
+}
+template void prolong_add<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
+                                  double*, const uint8_t*);
+template void prolong_add<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
+                                 float*, const uint8_t*);
+
+// ---------------------------------------------------------------------------------------------
+// coarsest level: dense assembly, Cholesky and triangular solves in one thread block
+// ---------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* A, T* diag0) {
+  // block = column j, threads = rows i
+  const int ncomp = physics == 0 ? 2 : 1;
+  const int nd = g.n * ncomp;
+  int col = blockIdx.x;
+  int nj = col / ncomp, cjc = col % ncomp;
+  int X2j, Y2j;
+  node_coords(g, nj, X2j, Y2j);
+  bool fj = is_fixed(g, X2j, Y2j, physics == 0 ? cjc : 2);
+  int NE = elems_per_cell(g.kind);
+  for (int row = threadIdx.x; row < nd; row += blockDim.x) {
+    int ni = row / ncomp, cic = row % ncomp;
+    int X2i, Y2i;
+    node_coords(g, ni, X2i, Y2i);
+    bool fi = is_fixed(g, X2i, Y2i, physics == 0 ? cic : 2);
+    double acc = 0.0;
+    if (fi || fj) {
+      acc = (row == col) ? 1.0 : 0.0;
+    } else {
+      for (int cell = 0; cell < g.ncell; ++cell) {
+        int cj = cell / g.nx, ci = cell - cj * g.nx;
+        for (int t = 0; t < NE; ++t) {
+          int nn[3];
+          cell_nodes(g, ci, cj, t, nn[0], nn[1], nn[2]);
+          int ki = -1, kj = -1;
+          for (int k = 0; k < 3; ++k) {
+            if (nn[k] == ni) ki = k;
+            if (nn[k] == nj) kj = k;
+          }
+          if (ki < 0 || kj < 0) continue;
+          double w = double(coef[cell * NE + t]) * g.area;
+          double gix = gxr(g.kind, t, ki) * g.ihx, giy = gyr(g.kind, t, ki) * g.ihy;
+          double gjx = gxr(g.kind, t, kj) * g.ihx, gjy = gyr(g.kind, t, kj) * g.ihy;
+          if (physics == 0) {
+            double v;
+            if (cic == 0 && cjc == 0) v = gix * gjx * m.lam2mu + giy * gjy * m.mu;
+            else if (cic == 0 && cjc == 1) v = gix * gjy * m.lam + giy * gjx * m.mu;
+            else if (cic == 1 && cjc == 0) v = giy * gjx * m.lam + gix * gjy * m.mu;
+            else v = giy * gjy * m.lam2mu + gix * gjx * m.mu;
+            acc += w * v;
+          } else {
+            acc += w * (ki == kj ? 2.0 : 1.0) / 12.0 + m.c1 * g.area * (gix * gjx + giy * gjy);
+          }
+        }
+      }
+    }
+    A[(size_t)row * nd + col] = T(acc);
+    if (row == col) diag0[row] = T(acc);
+  }
+}
+template <class T>
+void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef, T* A,
+                     T* diag0) {
+  int nd = g.n * (physics == 0 ? 2 : 1);
+  k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0);
+}
+template void coarse_assemble<double>(cudaStream_t, const Grid&, const Mat&, int, const double*,
+                                      double*, double*);
+template void coarse_assemble<float>(cudaStream_t, const Grid&, const Mat&, int, const float*,
+                                     float*, float*);
+
+// In-place Cholesky A = L L^T (lower triangle); a pivot that is not positive relative to the
+// original diagonal is replaced by that diagonal (a regularized factorization, acceptable for a
+// preconditioner when the coarse operator is singular).
+template <class T>
+__global__ void k_coarse_factor(int n, T* A, const T* diag0) {
+  __shared__ T piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      T d = A[(size_t)k * n + k];
+      T ref = diag0[k] > T(0) ? diag0[k] : T(1);
+      if (!(d > T(1e-10) * ref)) d = ref;
+      piv = sqrt(d);
+      A[(size_t)k * n + k] = piv;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= piv;
+    __syncthreads();
+    int m = n - k - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = k + 1 + idx / m, j = k + 1 + idx % m;
+      if (j <= i) A[(size_t)i * n + j] -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+    }
+    __syncthreads();
+  }
+}
+template <class T>
+void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0) {
+  k_coarse_factor<<<1, 1024, 0, s>>>(n, A, diag0);
+}
+template void coarse_factor<double>(cudaStream_t, int, double*, const double*);
+template void coarse_factor<float>(cudaStream_t, int, float*, const float*);
+
+template <class T>
+__global__ void k_coarse_solve(int n, const T* L, const T* b, T* x) {
+  extern __shared__ unsigned char smem_raw[];
+  T* y = reinterpret_cast<T*>(smem_raw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = b[i];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {  // forward: L y = b
+    if (threadIdx.x == 0) y[k] /= L[(size_t)k * n + k];
+    __syncthreads();
+    T yk = y[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= L[(size_t)i * n + k] * yk;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {  // backward: L^T x = y
+    if (threadIdx.x == 0) y[k] /= L[(size_t)k * n + k];
+    __syncthreads();
+    T yk = y[k];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] -= L[(size_t)k * n + i] * yk;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i];
+}
+template <class T>
+void coarse_solve(cudaStream_t s, int n, const T* L, const T* b, T* x) {
+  k_coarse_solve<<<1, 256, n * sizeof(T), s>>>(n, L, b, x);
+}
+template void coarse_solve<double>(cudaStream_t, int, const double*, const double*, double*);
+template void coarse_solve<float>(cudaStream_t, int, const float*, const float*, float*);
+
+// ---------------------------------------------------------------------------------------------
+// steepest-descent direction of ||Phi||^2 / 2 (Algorithm 4 fallback)
+// Phi_i = phi(x - l, psi), psi = phi(h - x, -F): dPhi/dx = pa - pb qa on the diagonal and
+// -pb qb H off it, with (pa, pb) = grad phi at (x - l, psi), (qa, qb) = grad phi at (h - x, -F).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void dphi(double a, double b, double& da, double& db) {
+  double r = sqrt(a * a + b * b);
+  if (r > 0.0) {
+    da = a / r - 1.0;
+    db = b / r - 1.0;
+  } else {
+    da = db = 1.0 / sqrt(2.0) - 1.0;
+  }
+}
+__global__ void k_merit_parts(Grid g, const double* x, const double* F, const double* lo, double* v,
+                              double* dg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  double l = lo[i], h = upper_of(g, i, l);
+  double xi = x[i], Fi = F[i];
+  double psi = phi_fb(h - xi, -Fi);
+  double ph = phi_fb(xi - l, psi);
+  double pa, pb, qa, qb;
+  dphi(xi - l, psi, pa, pb);
+  dphi(h - xi, -Fi, qa, qb);
+  v[i] = -pb * qb * ph;
+  dg[i] = (pa - pb * qa) * ph;
+}
+void merit_parts(cudaStream_t s, const Grid& g, const double* x, const double* F,
+                 const double* lo, double* v, double* dg) {
+  k_merit_parts<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, x, F, lo, v, dg);
+}
+__global__ void k_merit_dir(size_t n, const double* dg, const double* Hv, double* d) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) d[i] = -(dg[i] + Hv[i]);
+}
+void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d) {
+  k_merit_dir<<<nblocks(n), RED_THREADS, 0, s>>>(n, dg, Hv, d);
+}
+
+}  // namespace pf

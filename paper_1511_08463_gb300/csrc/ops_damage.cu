@@ -1,0 +1,53 @@
+// Launchers of the damage stencil operator H(q) and the damage gradient / MCP residual
+// (Section 1.2, eq. helmholtz; Section 2.4).
+#include "kernels.cuh"
+
+namespace pf {
+
+template <class Op>
+static void launch_op(cudaStream_t s, const Op& op) {
+  dim3 block(TX, TY);
+  dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
+  stencil_kernel<Op><<<grid, block, 0, s>>>(op);
+}
+
+template <class T, int K, int M, bool D>
+static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>& a) {
+  DamageOp<T, K, M, D> op;
+  op.g = g;
+  op.m = m;
+  op.args = a;
+  launch_op(s, op);
+}
+
+template <class T, int K>
+static void dispatch(cudaStream_t s, const Grid& g, const Mat& m, int mode, bool dot,
+                     const DamageArgs<T>& a) {
+  switch (mode) {
+    case M_APPLY: return go<T, K, M_APPLY, false>(s, g, m, a);
+    case M_MASKED:
+      return dot ? go<T, K, M_MASKED, true>(s, g, m, a) : go<T, K, M_MASKED, false>(s, g, m, a);
+    case M_RESB: return go<T, K, M_RESB, false>(s, g, m, a);
+    case M_CHEB: return go<T, K, M_CHEB, false>(s, g, m, a);
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (mode == M_GRAD) return go<T, K, M_GRAD, false>(s, g, m, a);
+    if (mode == M_TRIAL) return go<T, K, M_TRIAL, false>(s, g, m, a);
+  }
+}
+
+template <class T>
+void launch_damage(cudaStream_t s, const Grid& g, const Mat& m, int mode, bool dot,
+                   const DamageArgs<T>& a) {
+  if (g.kind == CROSSED)
+    dispatch<T, CROSSED>(s, g, m, mode, dot, a);
+  else
+    dispatch<T, RIGHT>(s, g, m, mode, dot, a);
+}
+
+template void launch_damage<double>(cudaStream_t, const Grid&, const Mat&, int, bool,
+                                    const DamageArgs<double>&);
+template void launch_damage<float>(cudaStream_t, const Grid&, const Mat&, int, bool,
+                                   const DamageArgs<float>&);
+
+}  // namespace pf

@@ -1,0 +1,63 @@
+// Launchers of the elasticity stencil operator K(alpha) (Section 1.2, eq. elasticity).
+#include "kernels.cuh"
+
+namespace pf {
+
+template <class Op>
+static void launch_op(cudaStream_t s, const Op& op) {
+  dim3 block(TX, TY);
+  dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
+  stencil_kernel<Op><<<grid, block, 0, s>>>(op);
+}
+
+template <class T, int K, int C, int M, bool E, bool D>
+static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>& a) {
+  ElasticOp<T, K, C, M, E, D> op;
+  op.g = g;
+  op.m = m;
+  op.args = a;
+  launch_op(s, op);
+}
+
+template <class T, int K>
+static void dispatch(cudaStream_t s, const Grid& g, const Mat& m, int coef, int mode, bool eigen,
+                     bool dot, const ElasticArgs<T>& a) {
+  if (coef == COEF_ALPHA) {
+    switch (mode) {
+      case M_APPLY: return go<T, K, COEF_ALPHA, M_APPLY, false, false>(s, g, m, a);
+      case M_MASKED:
+        return dot ? go<T, K, COEF_ALPHA, M_MASKED, false, true>(s, g, m, a)
+                   : go<T, K, COEF_ALPHA, M_MASKED, false, false>(s, g, m, a);
+      case M_RESB: return go<T, K, COEF_ALPHA, M_RESB, false, false>(s, g, m, a);
+      case M_RESID:
+        return eigen ? go<T, K, COEF_ALPHA, M_RESID, true, false>(s, g, m, a)
+                     : go<T, K, COEF_ALPHA, M_RESID, false, false>(s, g, m, a);
+      case M_CHEB: return go<T, K, COEF_ALPHA, M_CHEB, false, false>(s, g, m, a);
+    }
+  } else {
+    switch (mode) {
+      case M_APPLY: return go<T, K, COEF_ELEM, M_APPLY, false, false>(s, g, m, a);
+      case M_MASKED:
+        return dot ? go<T, K, COEF_ELEM, M_MASKED, false, true>(s, g, m, a)
+                   : go<T, K, COEF_ELEM, M_MASKED, false, false>(s, g, m, a);
+      case M_RESB: return go<T, K, COEF_ELEM, M_RESB, false, false>(s, g, m, a);
+      case M_CHEB: return go<T, K, COEF_ELEM, M_CHEB, false, false>(s, g, m, a);
+    }
+  }
+}
+
+template <class T>
+void launch_elastic(cudaStream_t s, const Grid& g, const Mat& m, int coef, int mode, bool eigen,
+                    bool dot, const ElasticArgs<T>& a) {
+  if (g.kind == CROSSED)
+    dispatch<T, CROSSED>(s, g, m, coef, mode, eigen, dot, a);
+  else
+    dispatch<T, RIGHT>(s, g, m, coef, mode, eigen, dot, a);
+}
+
+template void launch_elastic<double>(cudaStream_t, const Grid&, const Mat&, int, int, bool, bool,
+                                     const ElasticArgs<double>&);
+template void launch_elastic<float>(cudaStream_t, const Grid&, const Mat&, int, int, bool, bool,
+                                    const ElasticArgs<float>&);
+
+}  // namespace pf

@@ -1,0 +1,1119 @@
+// Host driver of libpf: hierarchy set-up, Krylov solvers, the reduced-space active-set damage
+// solve (Algorithm 4), over-relaxed alternate minimization (Algorithms 1-2) and the C ABI.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <new>
+#include <string>
+
+#include "solver.hpp"
+
+using namespace pf;
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+static thread_local std::string g_err;
+static pf_status fail(pf_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(PF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+#define TRY(expr)                    \
+  do {                               \
+    pf_status s_ = (expr);           \
+    if (s_ != PF_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// workspace arena
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct Arena {
+  char* base;
+  size_t cap, off = 0;
+  bool dry;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+constexpr int COARSE_TARGET_NODES = 128;
+constexpr int MAX_DENSE_DOFS = 320;
+
+bool pin_maps(int X2, int Y2, int kind) {
+  // a node of this level is also a node of the next coarser level
+  if ((X2 & 1) || (Y2 & 1)) return false;
+  int cx = X2 / 2, cy = Y2 / 2;
+  if ((cx & 1) != (cy & 1)) return false;
+  if ((cx & 1) && kind != CROSSED) return false;
+  return true;
+}
+
+Grid make_grid(const pf_mesh_desc& d, int level) {
+  Grid g;
+  memset(&g, 0, sizeof g);
+  int f = 1 << level;
+  g.kind = d.kind == PF_MESH_CROSSED ? CROSSED : RIGHT;
+  g.nx = d.nx / f;
+  g.ny = d.ny / f;
+  g.nv = (g.nx + 1) * (g.ny + 1);
+  g.ncell = g.nx * g.ny;
+  g.n = g.nv + (g.kind == CROSSED ? g.ncell : 0);
+  g.nelem = g.ncell * elems_per_cell(g.kind);
+  g.hx = d.lx / g.nx;
+  g.hy = d.ly / g.ny;
+  g.ihx = 1.0 / g.hx;
+  g.ihy = 1.0 / g.hy;
+  g.area = g.hx * g.hy / (g.kind == CROSSED ? 4.0 : 2.0);
+  for (int e = 0; e < 4; ++e)
+    for (int c = 0; c < 3; ++c) g.fixed[e][c] = d.fixed[e][c] ? 1 : 0;
+  g.npins = d.n_pins;
+  for (int k = 0; k < d.n_pins; ++k) {
+    g.pin_x2[k] = d.pin_x2[k] / f;
+    g.pin_y2[k] = d.pin_y2[k] / f;
+    g.pin_comp[k] = d.pin_comp[k];
+  }
+  return g;
+}
+
+pf_status validate(const pf_mesh_desc* d) {
+  if (!d) return fail(PF_EINVAL, "null mesh descriptor");
+  if (d->kind != PF_MESH_RIGHT && d->kind != PF_MESH_CROSSED)
+    return fail(PF_EINVAL, "unknown mesh kind %d", d->kind);
+  if (d->nx < 1 || d->ny < 1 || d->nx > 65536 || d->ny > 65536)
+    return fail(PF_EINVAL, "mesh size %d x %d out of range", d->nx, d->ny);
+  if (!(d->lx > 0) || !(d->ly > 0)) return fail(PF_EINVAL, "domain size must be positive");
+  if (d->n_pins < 0 || d->n_pins > PF_MAX_PINS) return fail(PF_EINVAL, "bad pin count");
+  if (d->n_boxes < 0 || d->n_boxes > PF_MAX_BOXES) return fail(PF_EINVAL, "bad box count");
+  for (int k = 0; k < d->n_pins; ++k) {
+    int X2 = d->pin_x2[k], Y2 = d->pin_y2[k];
+    bool vert = !(X2 & 1) && !(Y2 & 1), cen = (X2 & 1) && (Y2 & 1);
+    if (X2 < 0 || Y2 < 0 || X2 > 2 * d->nx || Y2 > 2 * d->ny || !(vert || (cen && d->kind == PF_MESH_CROSSED)))
+      return fail(PF_EINVAL, "pin %d is not a node", k);
+    if (d->pin_comp[k] < 0 || d->pin_comp[k] > 2) return fail(PF_EINVAL, "pin %d: bad component", k);
+  }
+  // corner agreement: edges sharing a corner and prescribing the same component
+  const int pairs[4][2] = {{0, 2}, {0, 3}, {1, 2}, {1, 3}};
+  for (auto& pr : pairs)
+    for (int c = 0; c < 3; ++c)
+      if (d->fixed[pr[0]][c] && d->fixed[pr[1]][c] && d->load[pr[0]][c] != d->load[pr[1]][c])
+        return fail(PF_EINVAL, "edges %d and %d prescribe different values at a corner", pr[0], pr[1]);
+  return PF_OK;
+}
+
+int count_levels(const pf_mesh_desc& d) {
+  int L = 1;
+  int nx = d.nx, ny = d.ny;
+  int kind = d.kind == PF_MESH_CROSSED ? CROSSED : RIGHT;
+  while (true) {
+    int nn = (nx + 1) * (ny + 1) + (kind == CROSSED ? nx * ny : 0);
+    if (nn <= COARSE_TARGET_NODES) break;
+    if ((nx & 1) || (ny & 1) || nx < 2 || ny < 2) break;
+    bool ok = true;
+    int f = 1 << (L - 1);
+    for (int k = 0; k < d.n_pins; ++k)
+      if (!pin_maps(d.pin_x2[k] / f, d.pin_y2[k] / f, kind)) ok = false;
+    if (!ok) break;
+    nx /= 2;
+    ny /= 2;
+    ++L;
+  }
+  return L;
+}
+
+template <class T>
+void take_level(Arena& a, Level& L, bool coarsest) {
+  const Grid& g = L.g;
+  LevelBuf<T>& B = L.buf<T>();
+  B.coefE = a.take<T>(g.nelem);
+  B.wD = a.take<T>(g.nelem);
+  B.dinvE = a.take<T>(2 * (size_t)g.n);
+  B.dinvD = a.take<T>(g.n);
+  B.b = a.take<T>(2 * (size_t)g.n);
+  B.x = a.take<T>(2 * (size_t)g.n);
+  B.r = a.take<T>(2 * (size_t)g.n);
+  B.xt = a.take<T>(2 * (size_t)g.n);
+  B.d = a.take<T>(2 * (size_t)g.n);
+  B.dt = a.take<T>(2 * (size_t)g.n);
+  if (coarsest && L.dense) {
+    size_t ne = 2 * (size_t)g.n, nd = g.n;
+    B.AE = a.take<T>(ne * ne);
+    B.AD = a.take<T>(nd * nd);
+    B.diagE = a.take<T>(ne);
+    B.diagD = a.take<T>(nd);
+  }
+}
+
+template <class T>
+void take_krylov(Arena& a, Krylov<T>& k, size_t n2) {
+  k.x = a.take<T>(n2);
+  k.r = a.take<T>(n2);
+  k.z = a.take<T>(n2);
+  k.p = a.take<T>(n2);
+  k.Ap = a.take<T>(n2);
+}
+
+void layout(pf_sim& s, Arena& a) {
+  const pf_mesh_desc& d = s.desc;
+  int L = count_levels(d);
+  s.lv.resize(L);
+  for (int l = 0; l < L; ++l) s.lv[l].g = make_grid(d, l);
+  Level& lc = s.lv[L - 1];
+  lc.dense = L > 1 && 2 * lc.g.n <= MAX_DENSE_DOFS;
+  const Grid& g = s.lv[0].g;
+  size_t n = g.n, n2 = 2 * n;
+  s.u = a.take<double>(n2);
+  s.alpha = a.take<double>(n);
+  s.alpha_prev = a.take<double>(n);
+  s.alpha32 = a.take<float>(n);
+  s.xu = a.take<double>(n2);
+  s.r64 = a.take<double>(n2);
+  s.q = a.take<double>(g.nelem);
+  s.eig = a.take<double>((size_t)g.ny * elems_per_cell(g.kind));
+  s.xrs = a.take<double>(n);
+  s.F = a.take<double>(n);
+  s.Phi = a.take<double>(n);
+  s.rhs = a.take<double>(n);
+  s.drs = a.take<double>(n);
+  s.xtr = a.take<double>(n);
+  s.Ftr = a.take<double>(n);
+  s.Phitr = a.take<double>(n);
+  s.rhstr = a.take<double>(n);
+  s.tmpa = a.take<double>(n2);
+  s.tmpb = a.take<double>(n2);
+  s.act = a.take<uint8_t>(n);
+  s.acttr = a.take<uint8_t>(n);
+  s.tmp32 = a.take<float>(n2);
+  take_krylov(a, s.k64, n2);
+  take_krylov(a, s.k32, n2);
+  for (int l = 0; l < L; ++l) {
+    take_level<double>(a, s.lv[l], l == L - 1);
+    take_level<float>(a, s.lv[l], l == L - 1);
+  }
+  size_t nb = ((size_t)(g.nx + 1 + TX - 1) / TX) * ((g.ny + 1 + TY - 1) / TY);
+  nb = std::max<size_t>(nb, MAX_RED_BLOCKS);
+  s.part = a.take<double>(nb * 4);
+  s.ticket = a.take<unsigned>(64);
+  s.scal = a.take<double>(S_COUNT);
+  s.ws_used = a.off;
+}
+
+inline RedSlot slot(pf_sim& s, int k) { return RedSlot{s.part, s.ticket, s.scal + k}; }
+
+pf_status read_scalars(pf_sim& s, cudaStream_t st, int k, int cnt, double* out) {
+  CU(cudaMemcpyAsync(s.ctx->host, s.scal + k, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  for (int i = 0; i < cnt; ++i) out[i] = s.ctx->host[i];
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// operators on level 0 and the multigrid hierarchy
+// ---------------------------------------------------------------------------------------------
+enum Physics { ELASTIC = 0, DAMAGE = 1 };
+
+template <class T>
+const T* alpha_of(pf_sim& s);
+template <>
+const double* alpha_of<double>(pf_sim& s) { return s.alpha; }
+template <>
+const float* alpha_of<float>(pf_sim& s) { return s.alpha32; }
+
+template <class T>
+Krylov<T>& kry(pf_sim& s);
+template <>
+Krylov<double>& kry<double>(pf_sim& s) { return s.k64; }
+template <>
+Krylov<float>& kry<float>(pf_sim& s) { return s.k32; }
+
+// y = A x on level l (masked operator of the free/inactive set), optional fused x.y
+template <class T>
+void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, bool dot, int sl) {
+  Level& L = s.lv[l];
+  if (phys == ELASTIC) {
+    ElasticArgs<T> a{};
+    a.x = x;
+    a.alpha = alpha_of<T>(s);
+    a.coef = L.buf<T>().coefE;
+    a.y = y;
+    a.slot = slot(s, sl);
+    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_MASKED, false, dot, a);
+  } else {
+    DamageArgs<T> a{};
+    a.x = x;
+    a.w = L.buf<T>().wD;
+    a.excl = l == 0 ? s.act : nullptr;
+    a.y = y;
+    a.slot = slot(s, sl);
+    launch_damage<T>(st, L.g, s.m, M_MASKED, dot, a);
+  }
+}
+
+template <class T>
+void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, T* r) {
+  Level& L = s.lv[l];
+  if (phys == ELASTIC) {
+    ElasticArgs<T> a{};
+    a.x = x;
+    a.alpha = alpha_of<T>(s);
+    a.coef = L.buf<T>().coefE;
+    a.b = b;
+    a.y = r;
+    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_RESB, false, false, a);
+  } else {
+    DamageArgs<T> a{};
+    a.x = x;
+    a.w = L.buf<T>().wD;
+    a.excl = l == 0 ? s.act : nullptr;
+    a.b = b;
+    a.y = r;
+    launch_damage<T>(st, L.g, s.m, M_RESB, false, a);
+  }
+}
+
+template <class T>
+void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, const T* d,
+               T* xo, T* dout, double cd, double cr) {
+  Level& L = s.lv[l];
+  if (phys == ELASTIC) {
+    ElasticArgs<T> a{};
+    a.x = x;
+    a.alpha = alpha_of<T>(s);
+    a.coef = L.buf<T>().coefE;
+    a.b = b;
+    a.d = d;
+    a.dinv = L.buf<T>().dinvE;
+    a.cd = T(cd);
+    a.cr = T(cr);
+    a.y = xo;
+    a.dout = dout;
+    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_CHEB, false, false, a);
+  } else {
+    DamageArgs<T> a{};
+    a.x = x;
+    a.w = L.buf<T>().wD;
+    a.excl = l == 0 ? s.act : nullptr;
+    a.b = b;
+    a.d = d;
+    a.dinv = L.buf<T>().dinvD;
+    a.cd = T(cd);
+    a.cr = T(cr);
+    a.y = xo;
+    a.dout = dout;
+    launch_damage<T>(st, L.g, s.m, M_CHEB, false, a);
+  }
+}
+
+// Chebyshev smoothing on D_l1^{-1} A over [lmin, lmax] = [0.1, 1] (l1 scaling bounds the
+// spectrum by 1).  Starts from x (x0 == nullptr: from zero); result written to x.
+template <class T>
+void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool from_zero,
+            int steps) {
+  LevelBuf<T>& B = s.lv[l].buf<T>();
+  const int nc = phys == ELASTIC ? 2 : 1;
+  const size_t nd = (size_t)nc * s.lv[l].g.n;
+  const double lmax = 1.0, lmin = 0.1;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (from_zero) vec_fill<T>(st, x, T(0), nd);
+  T *cx = x, *nx_ = B.xt, *cd_ = nullptr, *nd_ = B.d;
+  for (int k = 0; k < steps; ++k) {
+    double cdk, crk;
+    if (k == 0) {
+      cdk = 0.0;
+      crk = 1.0 / theta;
+    } else {
+      double rn = 1.0 / (2.0 * sigma - rho);
+      cdk = rn * rho;
+      crk = 2.0 * rn / delta;
+      rho = rn;
+    }
+    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk);
+    // rotate buffers: new x becomes current; the old current x buffer is free for the next step
+    T* ox = cx;
+    cx = nx_;
+    nx_ = ox;
+    T* od = cd_ ? cd_ : B.dt;
+    cd_ = nd_;
+    nd_ = od;
+  }
+  if (cx != x) cudaMemcpyAsync(x, cx, nd * sizeof(T), cudaMemcpyDeviceToDevice, st);
+}
+
+template <class T>
+void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int deg) {
+  Level& L = s.lv[l];
+  LevelBuf<T>& B = L.buf<T>();
+  const int nc = phys == ELASTIC ? 2 : 1;
+  const int nlev = (int)s.lv.size();
+  if (l == nlev - 1) {
+    if (L.dense && nlev > 1) {
+      coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AE : B.AD, b, x);
+    } else {
+      smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * deg : deg);
+    }
+    return;
+  }
+  Level& C = s.lv[l + 1];
+  LevelBuf<T>& BC = C.buf<T>();
+  smooth<T>(s, st, phys, l, b, x, true, deg);
+  residual_op<T>(s, st, phys, l, b, x, B.r);
+  restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b);
+  vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
+  prolong_add<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, BC.x, x,
+                 (phys == DAMAGE && l == 0) ? s.act : nullptr);
+  smooth<T>(s, st, phys, l, b, x, false, deg);
+}
+
+template <class T>
+void precond(pf_sim& s, cudaStream_t st, int phys, const T* r, T* z, int deg) {
+  const int nc = phys == ELASTIC ? 2 : 1;
+  if (s.lv.size() == 1) {
+    // single level: Chebyshev smoother alone
+    smooth<T>(s, st, phys, 0, r, z, true, deg);
+    (void)nc;
+    return;
+  }
+  vcycle<T>(s, st, phys, 0, r, z, deg);
+}
+
+// set up the coefficients, l1 diagonals and the coarsest factorization of one operator
+template <class T>
+void setup_elastic(pf_sim& s, cudaStream_t st) {
+  const int nlev = (int)s.lv.size();
+  elastic_coef<T>(st, s.lv[0].g, s.m, alpha_of<T>(s), s.lv[0].buf<T>().coefE);
+  for (int l = 1; l < nlev; ++l)
+    coarsen_coef<T>(st, s.lv[l - 1].g, s.lv[l].g, s.lv[l - 1].buf<T>().coefE, s.lv[l].buf<T>().coefE);
+  for (int l = 0; l < nlev; ++l)
+    l1_dinv_elastic<T>(st, s.lv[l].g, s.m, s.lv[l].buf<T>().coefE, s.lv[l].buf<T>().dinvE);
+  Level& Lc = s.lv[nlev - 1];
+  if (Lc.dense && nlev > 1) {
+    LevelBuf<T>& B = Lc.buf<T>();
+    coarse_assemble<T>(st, Lc.g, s.m, ELASTIC, B.coefE, B.AE, B.diagE);
+    coarse_factor<T>(st, 2 * Lc.g.n, B.AE, B.diagE);
+  }
+}
+
+template <class T>
+void setup_damage(pf_sim& s, cudaStream_t st) {
+  const int nlev = (int)s.lv.size();
+  for (int l = 1; l < nlev; ++l)
+    coarsen_coef<T>(st, s.lv[l - 1].g, s.lv[l].g, s.lv[l - 1].buf<T>().wD, s.lv[l].buf<T>().wD);
+  for (int l = 0; l < nlev; ++l)
+    l1_dinv_damage<T>(st, s.lv[l].g, s.m, s.lv[l].buf<T>().wD, s.lv[l].buf<T>().dinvD);
+  Level& Lc = s.lv[nlev - 1];
+  if (Lc.dense && nlev > 1) {
+    LevelBuf<T>& B = Lc.buf<T>();
+    coarse_assemble<T>(st, Lc.g, s.m, DAMAGE, B.wD, B.AD, B.diagD);
+    coarse_factor<T>(st, Lc.g.n, B.AD, B.diagD);
+  }
+}
+
+// Preconditioned CG for A_ff x = b (x starts at 0).  Stops when ||r|| <= rtol ||b||.
+template <class T>
+pf_status pcg(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, double rtol, int deg,
+              int64_t* iters, double* relres) {
+  Krylov<T>& K = kry<T>(s);
+  const int nc = phys == ELASTIC ? 2 : 1;
+  const size_t nd = (size_t)nc * s.lv[0].g.n;
+  vec_fill<T>(st, K.x, T(0), nd);
+  CU(cudaMemcpyAsync(K.r, b, nd * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  vec_dot<T>(st, K.r, K.r, nd, slot(s, S_RR));
+  double rr0;
+  TRY(read_scalars(s, st, S_RR, 1, &rr0));
+  if (!(rr0 == rr0) || isinf(rr0)) return fail(PF_ENUMERIC, "CG: right-hand side is not finite");
+  if (relres) *relres = 0.0;
+  if (rr0 == 0.0) return PF_OK;
+  const double tol2 = rtol * rtol * rr0;
+  precond<T>(s, st, phys, K.r, K.z, deg);
+  vec_dot<T>(st, K.r, K.z, nd, slot(s, S_RZ0));
+  cg_update_p<T>(st, K.p, K.z, nd, nullptr, nullptr);
+  int cur = 0;
+  double rr = rr0;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    apply_op<T>(s, st, phys, 0, K.p, K.Ap, true, S_PAP);
+    cg_update_xr<T>(st, K.x, K.r, K.p, K.Ap, nd, s.scal + (cur ? S_RZ1 : S_RZ0), s.scal + S_PAP,
+                    slot(s, S_RR));
+    TRY(read_scalars(s, st, S_RR, 1, &rr));
+    if (!(rr == rr)) return fail(PF_ENUMERIC, "CG breakdown (NaN residual)");
+    if (rr <= tol2) break;
+    precond<T>(s, st, phys, K.r, K.z, deg);
+    vec_dot<T>(st, K.r, K.z, nd, slot(s, cur ? S_RZ0 : S_RZ1));
+    cg_update_p<T>(st, K.p, K.z, nd, s.scal + (cur ? S_RZ0 : S_RZ1), s.scal + (cur ? S_RZ1 : S_RZ0));
+    cur ^= 1;
+  }
+  if (iters) *iters += std::min(it, maxit);
+  if (relres) *relres = sqrt(rr / rr0);
+  if (it > maxit) return fail(PF_ENOTCONV, "CG did not converge in %d iterations (rel. res. %.3e)",
+                              maxit, sqrt(rr / rr0));
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// load, eigenstrain, physical residual
+// ---------------------------------------------------------------------------------------------
+pf_status set_load(pf_sim& s, double t, double dT, cudaStream_t st) {
+  s.t = t;
+  s.dT = dT;
+  const Grid& g = s.lv[0].g;
+  lift_u(st, g, s.u, t, s.lift);
+  s.thermal = s.m.model && s.mat_in.beta != 0.0 && dT != 0.0;
+  if (s.thermal) {
+    int NE = elems_per_cell(g.kind);
+    std::vector<double> tab((size_t)g.ny * NE);
+    for (int j = 0; j < g.ny; ++j)
+      for (int t2 = 0; t2 < NE; ++t2) {
+        double y = (j + centroid_fy(g.kind, t2)) * g.hy;
+        tab[(size_t)j * NE + t2] = s.mat_in.beta * (-dT * erfc(y / s.mat_in.pen));
+      }
+    CU(cudaMemcpyAsync(s.eig, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  CU(cudaGetLastError());
+  s.elastic_ready64 = s.elastic_ready32 = false;
+  return PF_OK;
+}
+
+// r = f - K(alpha) u on free dofs (FP64); returns ||r||
+pf_status physical_residual(pf_sim& s, cudaStream_t st, const double* u, double* r, double* nrm) {
+  ElasticArgs<double> a{};
+  a.x = u;
+  a.alpha = s.alpha;
+  a.eig = s.eig;
+  a.y = r;
+  a.slot = slot(s, S_RES);
+  launch_elastic<double>(st, s.lv[0].g, s.m, COEF_ALPHA, M_RESID, s.thermal, false, a);
+  double v;
+  TRY(read_scalars(s, st, S_RES, 1, &v));
+  *nrm = sqrt(v);
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// u-subproblem: FP64 residual with FP64 PCG (PF_FP64) or FP32 PCG (PF_MIXED) corrections
+// ---------------------------------------------------------------------------------------------
+pf_status u_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
+  const Grid& g = s.lv[0].g;
+  const size_t n2 = 2 * (size_t)g.n;
+  const bool mixed = o.precision == PF_MIXED;
+  if (mixed ? !s.elastic_ready32 : !s.elastic_ready64) {
+    if (mixed) setup_elastic<float>(s, st);
+    else setup_elastic<double>(s, st);
+    (mixed ? s.elastic_ready32 : s.elastic_ready64) = true;
+  }
+  CU(cudaMemcpyAsync(s.xu, s.u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double rn;
+  TRY(physical_residual(s, st, s.xu, s.r64, &rn));
+  s.r_scale = std::max(s.r_scale, rn);
+  const double tol = o.u_rtol * s.r_scale;
+  for (int outer = 0; outer < 60; ++outer) {
+    if (rn <= tol || rn == 0.0) return PF_OK;
+    if (!(rn == rn)) return fail(PF_ENUMERIC, "u-subproblem residual is NaN");
+    if (rep) rep->outer_refinements++;
+    if (!mixed) {
+      double rel = std::max(tol / rn, 1e-15);
+      pf_status stt = pcg<double>(s, st, ELASTIC, s.r64, o.cg_maxit, rel, o.mg_degree,
+                                  rep ? &rep->cg_iters_u : nullptr, nullptr);
+      if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
+      vec_add<double>(st, s.xu, s.k64.x, n2);
+    } else {
+      vec_convert<float, double>(st, s.tmp32, s.r64, n2);
+      pf_status stt = pcg<float>(s, st, ELASTIC, s.tmp32, o.cg_maxit, o.inner_rtol, o.mg_degree,
+                                 rep ? &rep->cg_iters_u : nullptr, nullptr);
+      if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
+      vec_add_f32_to_f64(st, s.xu, s.k32.x, n2);
+    }
+    TRY(physical_residual(s, st, s.xu, s.r64, &rn));
+  }
+  if (rn <= tol || rn == 0.0) return PF_OK;
+  return fail(PF_ENOTCONV, "u-subproblem: residual %.3e above tolerance %.3e", rn, tol);
+}
+
+// ---------------------------------------------------------------------------------------------
+// damage subproblem: Algorithm 4 on the box [alpha_prev, 1]
+// ---------------------------------------------------------------------------------------------
+pf_status grad_at(pf_sim& s, cudaStream_t st, const double* x, double zeta, double* F, double* Phi,
+                  double* rhs, uint8_t* act, double out[2]) {
+  DamageArgs<double> a{};
+  a.x = x;
+  a.w = s.q;
+  a.lo = s.alpha_prev;
+  a.zeta = zeta;
+  a.y = F;
+  a.dout = Phi;
+  a.rhs = rhs;
+  a.act = act;
+  a.slot = slot(s, S_PHI);
+  launch_damage<double>(st, s.lv[0].g, s.m, M_GRAD, false, a);
+  return read_scalars(s, st, S_PHI, 2, out);
+}
+
+pf_status trial_at(pf_sim& s, cudaStream_t st, const double* x, const double* d, double mu,
+                   double zeta, double out[2]) {
+  DamageArgs<double> a{};
+  a.x = x;
+  a.d = d;
+  a.cd = mu;
+  a.w = s.q;
+  a.lo = s.alpha_prev;
+  a.zeta = zeta;
+  a.y = s.Ftr;
+  a.dout = s.Phitr;
+  a.rhs = s.rhstr;
+  a.act = s.acttr;
+  a.xt = s.xtr;
+  a.slot = slot(s, S_PHI);
+  launch_damage<double>(st, s.lv[0].g, s.m, M_TRIAL, false, a);
+  return read_scalars(s, st, S_PHI, 2, out);
+}
+
+void damage_prepare(pf_sim& s, cudaStream_t st, bool mixed) {
+  const Grid& g = s.lv[0].g;
+  damage_q(st, g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, s.lv[0].f64.wD,
+           mixed ? s.lv[0].f32.wD : nullptr);
+  if (mixed) setup_damage<float>(s, st);
+  else setup_damage<double>(s, st);
+}
+
+pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
+  const Grid& g = s.lv[0].g;
+  const size_t n = g.n;
+  const bool mixed = o.precision == PF_MIXED;
+  damage_prepare(s, st, mixed);
+  CU(cudaMemcpyAsync(s.xrs, s.alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double v[2];
+  TRY(grad_at(s, st, s.xrs, o.zeta, s.F, s.Phi, s.rhs, s.act, v));
+  double phi2 = v[0];
+  double phi0 = sqrt(phi2);
+  s.phi_scale = std::max(s.phi_scale, phi0);
+  const double tol = o.rs_rtol * s.phi_scale;
+  const double c_armijo = 1e-4;
+  int it = 0;
+  for (;;) {
+    double phi = sqrt(phi2);
+    if (!(phi == phi)) return fail(PF_ENUMERIC, "damage residual is NaN");
+    if (phi <= tol || phi2 == 0.0) break;
+    if (it >= o.rs_maxit) return fail(PF_ENOTCONV, "damage solve: %d iterations, ||Phi|| %.3e > %.3e",
+                                      it, phi, tol);
+    ++it;
+    // reduced Newton step on the inactive set: H_NN d_N = -F_N, d_A = 0 (eq. reducednewton)
+    if (!mixed) {
+      pf_status stt = pcg<double>(s, st, DAMAGE, s.rhs, o.cg_maxit, o.alpha_cg_rtol, o.mg_degree,
+                                  rep ? &rep->cg_iters_alpha : nullptr, nullptr);
+      if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
+      CU(cudaMemcpyAsync(s.drs, s.k64.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      vec_convert<float, double>(st, s.tmp32, s.rhs, n);
+      pf_status stt = pcg<float>(s, st, DAMAGE, s.tmp32, o.cg_maxit, o.alpha_cg_rtol, o.mg_degree,
+                                 rep ? &rep->cg_iters_alpha : nullptr, nullptr);
+      if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
+      vec_convert<double, float>(st, s.drs, s.k32.x, n);
+    }
+    // projected line search on ||Phi||^2; steepest descent of the merit function if it fails
+    bool accepted = false;
+    for (int dir = 0; dir < 2 && !accepted; ++dir) {
+      if (dir == 1) {
+        merit_parts(st, g, s.xrs, s.F, s.alpha_prev, s.tmpa, s.tmpb);
+        DamageArgs<double> a{};
+        a.x = s.tmpa;
+        a.w = s.lv[0].f64.wD;
+        a.y = s.tmpa + n;
+        launch_damage<double>(st, g, s.m, M_APPLY, false, a);
+        merit_direction(st, n, s.tmpb, s.tmpa + n, s.drs);
+      }
+      for (double mu = 1.0; mu >= 0x1p-20; mu *= 0.5) {
+        double w[2];
+        TRY(trial_at(s, st, s.xrs, s.drs, mu, o.zeta, w));
+        if (w[0] <= (1.0 - 2.0 * c_armijo * mu) * phi2) {
+          std::swap(s.xrs, s.xtr);
+          std::swap(s.F, s.Ftr);
+          std::swap(s.Phi, s.Phitr);
+          std::swap(s.rhs, s.rhstr);
+          std::swap(s.act, s.acttr);
+          phi2 = w[0];
+          accepted = true;
+          break;
+        }
+      }
+    }
+    if (!accepted) return fail(PF_ENOTCONV, "damage solve: line search failed at ||Phi|| %.3e", phi);
+  }
+  if (rep) rep->rs_iters += it;
+  return PF_OK;
+}
+
+// first candidate of omega, (1+omega)/2, ... not above the largest feasible step (Section 2.1)
+double choose_omega_bar(double omega, double wstar) {
+  if (omega <= 1.0) return omega;
+  double w = omega;
+  for (int k = 0; k <= 30; ++k) {
+    if (w <= wstar) return w;
+    w = 0.5 * (1.0 + w);
+  }
+  return 1.0;
+}
+
+pf_status energy_now(pf_sim& s, cudaStream_t st, double out[3]) {
+  energy(st, s.lv[0].g, s.m, s.u, s.alpha, s.thermal ? s.eig : nullptr, slot(s, S_EN));
+  double v[2];
+  TRY(read_scalars(s, st, S_EN, 2, v));
+  out[0] = v[0];
+  out[1] = v[1];
+  out[2] = v[0] + v[1];
+  return PF_OK;
+}
+
+pf_status full_residual(pf_sim& s, cudaStream_t st, double zeta, double* nrm) {
+  double rn;
+  TRY(physical_residual(s, st, s.u, s.r64, &rn));
+  damage_q(st, s.lv[0].g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, nullptr, nullptr);
+  double v[2];
+  TRY(grad_at(s, st, s.alpha, zeta, s.Ftr, s.Phitr, s.rhstr, s.acttr, v));
+  *nrm = sqrt(rn * rn + v[0]);
+  return PF_OK;
+}
+
+pf_status begin_step(pf_sim& s, cudaStream_t st, const pf_load& L) {
+  const size_t n = s.lv[0].g.n;
+  CU(cudaMemcpyAsync(s.alpha_prev, s.alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(set_load(s, L.t, L.dT, st));
+  s.r_scale = 0.0;
+  s.phi_scale = 0.0;
+  return PF_OK;
+}
+
+pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
+  const Grid& g = s.lv[0].g;
+  const size_t n2 = 2 * (size_t)g.n;
+  const double omega = o.algo == PF_ALGO_AM ? 1.0 : o.omega;
+  pf_status last = PF_ENOTCONV;
+  for (int k = 1; k <= o.am_maxit; ++k) {
+    pf_status st1 = u_solve(s, st, o, rep);
+    if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
+    relax_u(st, s.u, s.xu, omega, n2, slot(s, S_DU));
+    double du[2];
+    TRY(read_scalars(s, st, S_DU, 2, du));
+    pf_status st2 = alpha_solve(s, st, o, rep);
+    if (st2 != PF_OK && st2 != PF_ENOTCONV) return st2;
+    omega_star(st, g, s.alpha, s.xrs, s.alpha_prev, slot(s, S_OMEGA));
+    double ms;
+    TRY(read_scalars(s, st, S_OMEGA, 1, &ms));
+    double wbar = choose_omega_bar(omega, -ms);
+    relax_alpha(st, g, s.alpha, s.xrs, s.alpha_prev, wbar, s.alpha32, slot(s, S_DALPHA));
+    double da;
+    TRY(read_scalars(s, st, S_DALPHA, 1, &da));
+    if (da > 0.0) s.elastic_ready64 = s.elastic_ready32 = false;
+    double durel = du[1] > 0.0 ? du[0] / du[1] : du[0];
+    if (rep) {
+      rep->am_iters = k;
+      rep->dalpha_inf = da;
+      rep->du_rel = durel;
+      rep->omega_bar_min = std::min(rep->omega_bar_min, wbar);
+    }
+    if (da <= o.am_tol && durel <= o.am_tol) {
+      last = PF_OK;
+      break;
+    }
+  }
+  return last;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char* pf_last_error(void) { return g_err.c_str(); }
+const char* pf_version(void) { return "libpf 0.1 (sm_103a)"; }
+
+pf_status pf_default_opts(pf_solver_opts* o) {
+  if (!o) return fail(PF_EINVAL, "null options");
+  memset(o, 0, sizeof *o);
+  o->algo = PF_ALGO_ORAM;
+  o->precision = PF_FP64;
+  o->omega = 1.0;
+  o->am_tol = 1e-6;
+  o->am_maxit = 2000;
+  o->u_rtol = 1e-8;
+  o->inner_rtol = 1e-4;
+  o->cg_maxit = 2000;
+  o->rs_rtol = 1e-8;
+  o->rs_maxit = 100;
+  o->alpha_cg_rtol = 1e-6;
+  o->zeta = 1e-10;
+  o->mg_levels_max = 0;
+  o->mg_degree = 2;
+  o->switch_tol = 1e-2;
+  o->newton_rtol = 1e-8;
+  o->newton_maxit = 30;
+  o->minres_maxit = 500;
+  o->minres_rtol = 1e-6;
+  o->use_graphs = 0;
+  return PF_OK;
+}
+
+pf_status pf_ctx_create(int device, pf_ctx** out) {
+  if (!out) return fail(PF_EINVAL, "null output");
+  CU(cudaSetDevice(device));
+  pf_ctx* c = new (std::nothrow) pf_ctx;
+  if (!c) return fail(PF_ENOMEM, "host allocation failed");
+  c->device = device;
+  cudaError_t e = cudaMallocHost(&c->host, 64 * sizeof(double));
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(PF_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return PF_OK;
+}
+
+void pf_ctx_destroy(pf_ctx* c) {
+  if (!c) return;
+  if (c->host) cudaFreeHost(c->host);
+  delete c;
+}
+
+size_t pf_workspace_bytes(const pf_mesh_desc* d, int precision) {
+  (void)precision;
+  if (validate(d) != PF_OK) return 0;
+  pf_sim s;
+  s.desc = *d;
+  Arena a{nullptr, 0, 0, true};
+  layout(s, a);
+  return a.off + 256;
+}
+
+pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_bytes,
+                         pf_sim** out) {
+  if (!ctx || !out) return fail(PF_EINVAL, "null argument");
+  TRY(validate(d));
+  if (!ws) return fail(PF_EINVAL, "null workspace");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(PF_EINVAL, "workspace not 256-byte aligned");
+  size_t need = pf_workspace_bytes(d, PF_FP64);
+  if (ws_bytes < need) return fail(PF_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+  CU(cudaSetDevice(ctx->device));
+  pf_sim* s = new (std::nothrow) pf_sim;
+  if (!s) return fail(PF_ENOMEM, "host allocation failed");
+  s->ctx = ctx;
+  s->desc = *d;
+  Arena a{static_cast<char*>(ws), ws_bytes, 0, false};
+  layout(*s, a);
+  for (int e = 0; e < 4; ++e)
+    for (int c = 0; c < 3; ++c) s->lift.load[e][c] = d->load[e][c];
+  for (int k = 0; k < d->n_pins; ++k) s->lift.pin_load[k] = d->pin_load[k];
+  // initial state on the host: u = 0, alpha = alpha_prev from the damage boxes and the damage
+  // Dirichlet data
+  const Grid& g = s->lv[0].g;
+  std::vector<double> al(g.n, 0.0);
+  for (int node = 0; node < g.n; ++node) {
+    int X2, Y2;
+    if (node < g.nv) {
+      int j = node / (g.nx + 1), i = node - j * (g.nx + 1);
+      X2 = 2 * i;
+      Y2 = 2 * j;
+    } else {
+      int c = node - g.nv, j = c / g.nx, i = c - j * g.nx;
+      X2 = 2 * i + 1;
+      Y2 = 2 * j + 1;
+    }
+    for (int b = 0; b < d->n_boxes; ++b)
+      if (X2 >= d->box[b][0] && X2 <= d->box[b][1] && Y2 >= d->box[b][2] && Y2 <= d->box[b][3])
+        al[node] = d->box_value[b];
+    const int eX[4] = {0, 2 * g.nx, -1, -1}, eY[4] = {-1, -1, 0, 2 * g.ny};
+    for (int e = 0; e < 4; ++e)
+      if (d->fixed[e][2] && ((eX[e] >= 0 && X2 == eX[e]) || (eY[e] >= 0 && Y2 == eY[e])))
+        al[node] = d->load[e][2];
+    for (int k = 0; k < d->n_pins; ++k)
+      if (d->pin_comp[k] == 2 && d->pin_x2[k] == X2 && d->pin_y2[k] == Y2) al[node] = d->pin_load[k];
+  }
+  std::vector<float> al32(al.begin(), al.end());
+  cudaError_t e1 = cudaMemset(s->u, 0, 2 * (size_t)g.n * sizeof(double));
+  cudaError_t e2 = cudaMemcpy(s->alpha, al.data(), g.n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaError_t e3 = cudaMemcpy(s->alpha_prev, al.data(), g.n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaError_t e4 = cudaMemcpy(s->alpha32, al32.data(), g.n * sizeof(float), cudaMemcpyHostToDevice);
+  cudaError_t e5 = cudaMemset(s->ticket, 0, 64 * sizeof(unsigned));
+  cudaError_t e6 = cudaMemset(s->eig, 0, (size_t)g.ny * elems_per_cell(g.kind) * sizeof(double));
+  cudaError_t e7 = cudaDeviceSynchronize();
+  for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7})
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(PF_ECUDA, "initial state upload: %s", cudaGetErrorString(e));
+    }
+  *out = s;
+  return PF_OK;
+}
+
+pf_status pf_set_material(pf_sim* s, const pf_material* mi) {
+  if (!s || !mi) return fail(PF_EINVAL, "null argument");
+  if (!(mi->E > 0) || !(mi->Gc > 0) || !(mi->ell > 0) || !(mi->k_ell >= 0) || !(mi->nu > -1.0) ||
+      !(mi->nu < 0.5))
+    return fail(PF_EINVAL, "invalid material constants");
+  if (mi->model != PF_AT1 && mi->model != PF_AT2) return fail(PF_EINVAL, "unknown damage model");
+  if (mi->plane != PF_PLANE_STRAIN && mi->plane != PF_PLANE_STRESS)
+    return fail(PF_EINVAL, "unknown plane assumption");
+  if (mi->beta != 0.0 && !(mi->pen > 0)) return fail(PF_EINVAL, "penetration length must be positive");
+  Mat m{};
+  double E = mi->E, nu = mi->nu;
+  m.mu = E / (2.0 * (1.0 + nu));
+  m.lam = mi->plane == PF_PLANE_STRAIN ? E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) : E * nu / (1.0 - nu * nu);
+  m.lam2mu = m.lam + 2.0 * m.mu;
+  m.k_ell = mi->k_ell;
+  double cw = mi->model == PF_AT1 ? 8.0 / 3.0 : 2.0;  // c_w = 4 int_0^1 sqrt(w)
+  m.c1 = 2.0 * mi->Gc * mi->ell / cw;
+  m.c2 = mi->model == PF_AT2 ? 2.0 * mi->Gc / (cw * mi->ell) : 0.0;
+  m.c3 = mi->model == PF_AT1 ? mi->Gc / (cw * mi->ell) : 0.0;
+  m.gc_cw = mi->Gc / cw;
+  m.ell = mi->ell;
+  m.model = mi->model;
+  s->m = m;
+  s->mat_in = *mi;
+  s->have_material = true;
+  s->elastic_ready64 = s->elastic_ready32 = false;
+  return PF_OK;
+}
+
+static pf_status check_opts(const pf_solver_opts* o) {
+  if (!o) return fail(PF_EINVAL, "null options");
+  if (o->algo < PF_ALGO_AM || o->algo > PF_ALGO_ORAM_N) return fail(PF_EINVAL, "unknown algorithm");
+  if (o->precision != PF_FP64 && o->precision != PF_MIXED) return fail(PF_EINVAL, "unknown precision");
+  if (!(o->omega > 0.0 && o->omega < 2.0)) return fail(PF_EINVAL, "omega must lie in (0, 2)");
+  if (o->am_maxit < 1 || o->cg_maxit < 1 || o->rs_maxit < 1 || o->mg_degree < 1)
+    return fail(PF_EINVAL, "iteration limits must be positive");
+  return PF_OK;
+}
+
+pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, void* stream,
+                       pf_step_report* rep) {
+  if (!s || !L) return fail(PF_EINVAL, "null argument");
+  TRY(check_opts(o));
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  if (s->busy) return fail(PF_EBUSY, "sim busy");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  s->busy = true;
+  auto t0 = std::chrono::steady_clock::now();
+  pf_step_report r{};
+  r.omega_bar_min = o->omega;
+  pf_status status = begin_step(*s, st, *L);
+  if (status == PF_OK) status = oram_step(*s, st, *o, &r);
+  if (status == PF_OK || status == PF_ENOTCONV) {
+    pf_status e2 = energy_now(*s, st, r.energy);
+    if (e2 != PF_OK) status = e2;
+  }
+  r.status = status;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rep) *rep = r;
+  s->busy = false;
+  return status;
+}
+
+pf_status pf_energy(pf_sim* s, void* stream, double out[3]) {
+  if (!s || !out) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  CU(cudaSetDevice(s->ctx->device));
+  return energy_now(*s, static_cast<cudaStream_t>(stream), out);
+}
+
+pf_status pf_solve_batch(pf_ctx* ctx, pf_sim* const* sims, const pf_load* loads, int n,
+                         const pf_solver_opts* o, void* stream, pf_step_report* reps) {
+  if (!ctx || (n > 0 && (!sims || !loads))) return fail(PF_EINVAL, "null argument");
+  pf_status worst = PF_OK;
+  for (int i = 0; i < n; ++i) {
+    pf_status st = pf_load_step(sims[i], &loads[i], o, stream, reps ? &reps[i] : nullptr);
+    if (st > worst) worst = st;
+  }
+  return worst;
+}
+
+pf_status pf_get_fields(pf_sim* s, double* u, double* alpha, double* alpha_prev) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  CU(cudaSetDevice(s->ctx->device));
+  CU(cudaDeviceSynchronize());
+  size_t n = s->lv[0].g.n;
+  if (u) CU(cudaMemcpy(u, s->u, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (alpha) CU(cudaMemcpy(alpha, s->alpha, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (alpha_prev) CU(cudaMemcpy(alpha_prev, s->alpha_prev, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return PF_OK;
+}
+
+pf_status pf_set_fields(pf_sim* s, const double* u, const double* alpha, const double* alpha_prev) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  CU(cudaSetDevice(s->ctx->device));
+  size_t n = s->lv[0].g.n;
+  if (u) CU(cudaMemcpy(s->u, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice));
+  if (alpha) {
+    CU(cudaMemcpy(s->alpha, alpha, n * sizeof(double), cudaMemcpyHostToDevice));
+    vec_convert<float, double>(0, s->alpha32, s->alpha, n);
+  }
+  if (alpha_prev) CU(cudaMemcpy(s->alpha_prev, alpha_prev, n * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaDeviceSynchronize());
+  s->elastic_ready64 = s->elastic_ready32 = false;
+  return PF_OK;
+}
+
+pf_status pf_sim_info(const pf_sim* s, int64_t* n_nodes, int64_t* n_elements, int32_t* levels) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  if (n_nodes) *n_nodes = s->lv[0].g.n;
+  if (n_elements) *n_elements = s->lv[0].g.nelem;
+  if (levels) *levels = (int32_t)s->lv.size();
+  return PF_OK;
+}
+
+void pf_destroy(pf_sim* s) { delete s; }
+
+pf_status pf_set_load(pf_sim* s, const pf_load* L) {
+  if (!s || !L) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  CU(cudaSetDevice(s->ctx->device));
+  TRY(set_load(*s, L->t, L->dT, 0));
+  CU(cudaDeviceSynchronize());
+  return PF_OK;
+}
+
+pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* x, void* y,
+                              void* stream) {
+  if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  const int mode = masked ? M_MASKED : M_APPLY;
+  if (precision == PF_FP64) {
+    ElasticArgs<double> a{};
+    a.x = static_cast<const double*>(x);
+    a.alpha = s->alpha;
+    a.y = static_cast<double*>(y);
+    launch_elastic<double>(st, s->lv[0].g, s->m, COEF_ALPHA, mode, false, false, a);
+  } else if (precision == PF_MIXED) {
+    ElasticArgs<float> a{};
+    a.x = static_cast<const float*>(x);
+    a.alpha = s->alpha32;
+    a.y = static_cast<float*>(y);
+    launch_elastic<float>(st, s->lv[0].g, s->m, COEF_ALPHA, mode, false, false, a);
+  } else {
+    return fail(PF_EINVAL, "unknown precision");
+  }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+pf_status pf_op_elastic_residual(pf_sim* s, double* r, double* norm2, void* stream) {
+  if (!s || !r) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  CU(cudaSetDevice(s->ctx->device));
+  double nrm;
+  TRY(physical_residual(*s, static_cast<cudaStream_t>(stream), s->u, r, &nrm));
+  if (norm2) *norm2 = nrm * nrm;
+  return PF_OK;
+}
+
+pf_status pf_op_damage_gradient(pf_sim* s, double* F, double* Phi, uint8_t* active,
+                                double* phi_norm2, void* stream) {
+  if (!s || !F || !Phi) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  damage_q(st, s->lv[0].g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, nullptr, nullptr);
+  double v[2];
+  TRY(grad_at(*s, st, s->alpha, 1e-10, F, Phi, s->rhstr, active ? active : s->acttr, v));
+  if (phi_norm2) *phi_norm2 = v[0];
+  return PF_OK;
+}
+
+pf_status pf_op_damage_apply(pf_sim* s, int precision, const void* x, void* y, void* stream) {
+  if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  const Grid& g = s->lv[0].g;
+  damage_q(st, g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, s->lv[0].f64.wD, s->lv[0].f32.wD);
+  if (precision == PF_FP64) {
+    DamageArgs<double> a{};
+    a.x = static_cast<const double*>(x);
+    a.w = s->lv[0].f64.wD;
+    a.y = static_cast<double*>(y);
+    launch_damage<double>(st, g, s->m, M_APPLY, false, a);
+  } else if (precision == PF_MIXED) {
+    DamageArgs<float> a{};
+    a.x = static_cast<const float*>(x);
+    a.w = s->lv[0].f32.wD;
+    a.y = static_cast<float*>(y);
+    launch_damage<float>(st, g, s->m, M_APPLY, false, a);
+  } else {
+    return fail(PF_EINVAL, "unknown precision");
+  }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_step_report* rep) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  TRY(check_opts(o));
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  s->r_scale = 0.0;
+  s->elastic_ready64 = s->elastic_ready32 = false;
+  pf_step_report r{};
+  pf_status status = u_solve(*s, st, *o, &r);
+  if (status == PF_OK || status == PF_ENOTCONV)
+    CU(cudaMemcpyAsync(s->u, s->xu, 2 * (size_t)s->lv[0].g.n * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  if (rep) *rep = r;
+  return status;
+}
+
+pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_step_report* rep) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  TRY(check_opts(o));
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  s->phi_scale = 0.0;
+  pf_step_report r{};
+  pf_status status = alpha_solve(*s, st, *o, &r);
+  if (status == PF_OK || status == PF_ENOTCONV) {
+    const size_t n = s->lv[0].g.n;
+    CU(cudaMemcpyAsync(s->alpha, s->xrs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    vec_convert<float, double>(st, s->alpha32, s->alpha, n);
+    s->elastic_ready64 = s->elastic_ready32 = false;
+  }
+  CU(cudaStreamSynchronize(st));
+  if (rep) *rep = r;
+  return status;
+}
+
+pf_status pf_op_full_residual(pf_sim* s, double* phi_norm, void* stream) {
+  if (!s || !phi_norm) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  CU(cudaSetDevice(s->ctx->device));
+  return full_residual(*s, static_cast<cudaStream_t>(stream), 1e-10, phi_norm);
+}
+
+}  // extern "C"

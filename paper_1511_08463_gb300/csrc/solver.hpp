@@ -1,0 +1,88 @@
+// Host-side data structures of libpf: the sim, its multigrid hierarchy and work buffers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct pf_ctx {
+  int device;
+  double* host;  // pinned scratch for scalar read-back (64 doubles)
+};
+
+namespace pf {
+
+template <class T>
+struct LevelBuf {
+  T* coefE = nullptr;   // elastic abar per element
+  T* dinvE = nullptr;   // inverse l1 diagonal (2n)
+  T* wD = nullptr;      // damage mass weight per element
+  T* dinvD = nullptr;   // (n)
+  T *b = nullptr, *x = nullptr, *r = nullptr, *xt = nullptr, *d = nullptr, *dt = nullptr;  // 2n
+  T *AE = nullptr, *AD = nullptr, *diagE = nullptr, *diagD = nullptr;  // coarsest dense
+};
+
+struct Level {
+  Grid g;
+  LevelBuf<double> f64;
+  LevelBuf<float> f32;
+  bool dense = false;  // coarsest level solved by dense Cholesky
+  template <class T>
+  LevelBuf<T>& buf();
+};
+template <>
+inline LevelBuf<double>& Level::buf<double>() { return f64; }
+template <>
+inline LevelBuf<float>& Level::buf<float>() { return f32; }
+
+template <class T>
+struct Krylov {
+  T *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+};
+
+// scalar slots in device memory
+enum Slot {
+  S_RR = 0, S_RZ0 = 1, S_RZ1 = 2, S_PAP = 3, S_RES = 4, S_DU = 5,   // S_DU: 2 values
+  S_OMEGA = 8, S_DALPHA = 9, S_PHI = 10,                            // S_PHI: 2 values
+  S_EN = 12,                                                         // 2 values
+  S_TMP = 16, S_COUNT = 32
+};
+
+}  // namespace pf
+
+struct pf_sim {
+  pf_ctx* ctx = nullptr;
+  pf_mesh_desc desc;
+  pf::Mat m;
+  bool have_material = false;
+  pf_material mat_in;
+  std::vector<pf::Level> lv;
+  pf::LiftData lift;
+  double t = 0.0, dT = 0.0;
+  bool thermal = false;  // eigenstrain table valid and nonzero
+  // resident state (FP64)
+  double *u = nullptr, *alpha = nullptr, *alpha_prev = nullptr;
+  float* alpha32 = nullptr;
+  // FP64 work
+  double *xu = nullptr, *r64 = nullptr, *q = nullptr, *eig = nullptr;
+  double *xrs = nullptr, *F = nullptr, *Phi = nullptr, *rhs = nullptr, *drs = nullptr;
+  double *xtr = nullptr, *Ftr = nullptr, *Phitr = nullptr, *rhstr = nullptr;
+  double *tmpa = nullptr, *tmpb = nullptr;
+  uint8_t *act = nullptr, *acttr = nullptr;
+  float* tmp32 = nullptr;
+  pf::Krylov<double> k64;
+  pf::Krylov<float> k32;
+  // reductions
+  double* part = nullptr;
+  unsigned* ticket = nullptr;
+  double* scal = nullptr;
+  // per-step tolerance scales
+  double r_scale = 0.0, phi_scale = 0.0;
+  // MG state validity
+  bool elastic_ready64 = false, elastic_ready32 = false, damage_ready64 = false,
+       damage_ready32 = false;
+  size_t ws_used = 0;
+  bool busy = false;
+};

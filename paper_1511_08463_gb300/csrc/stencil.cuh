@@ -1,0 +1,378 @@
+// Matrix-free P1 operators on structured triangulations, in cell-tiled stencil form.
+//
+// One thread block owns a tile of TX x TY vertices (and, on crossed meshes, the TX x TY cell
+// centres with the same indices).  It stages the node values of the tile plus a one-node halo in
+// shared memory, computes one record per element of the (TX+1) x (TY+1) cells that touch the
+// tile (each element exactly once per block, no atomics), and every thread then gathers the
+// contributions of the elements around its vertex (6 on right meshes, 8 on crossed meshes) and
+// its centre (4) in a fixed order, so results are bitwise reproducible.
+//
+// Operators (Section 1.2 second derivatives, P1 exact integration):
+//   ElasticOp: K(alpha) u = sum_T w_T B_T^T A0 (B_T u_T - eps0_T), w_T = abar_T |T|,
+//              abar_T = (1/|T|) int_T (1 - alpha_h)^2 + k_ell (eq. elasticity; eigenstrain of
+//              eq. energytshock for the physical residual).
+//   DamageOp:  H p = sum_T (w_T M_T + c1 L_T) p_T with w_T = q_T + c2 (eq. helmholtz), and for
+//              the gradient E_alpha = H alpha + g0, g0_T = (c3 - q_T) |T| / 3 per node.
+#pragma once
+#include "pf_core.cuh"
+
+namespace pf {
+
+enum Mode : int {
+  M_APPLY = 0,   // y = A x
+  M_MASKED = 1,  // y = A_ff x_f on free dofs (x read as 0 on excluded dofs), 0 on excluded dofs
+  M_RESB = 2,    // r = b - A_ff x_f on free dofs, 0 on excluded dofs
+  M_RESID = 3,   // elastic physical residual r = f - K u on free dofs (u unmasked), 0 elsewhere
+  M_CHEB = 4,    // Chebyshev step: d' = cd d + cr dinv (b - A x); x' = x + d' (free dofs)
+  M_GRAD = 5,    // damage: F = H x + g0, Phi, active flags, rhs = -F on the inactive set
+  M_TRIAL = 6    // damage: same as M_GRAD at x_t = clip(x + mu d, lo, hi); writes x_t
+};
+
+template <class T>
+struct V2 {
+  T x, y;
+};
+
+// ----------------------------------------------------------------------------------------------
+// generic tile kernel
+// ----------------------------------------------------------------------------------------------
+template <class Op>
+__global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
+  using V = typename Op::V;
+  using R = typename Op::R;
+  constexpr int KIND = Op::KIND;
+  constexpr int NE = elems_per_cell(KIND);
+  constexpr int NC = KIND == CROSSED ? TY + 1 : 1;
+  __shared__ V sv[TY + 2][TX + 2];
+  __shared__ V sc[NC][TX + 1];
+  __shared__ R se[TY + 1][TX + 1][NE];
+  const Grid& g = op.g;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + ty * TX;
+
+  for (int s = tid; s < (TX + 2) * (TY + 2); s += TX * TY) {
+    int li = s % (TX + 2), lj = s / (TX + 2);
+    int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+    bool in = gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny;
+    sv[lj][li] = in ? op.load(gj * (g.nx + 1) + gi, 2 * gi, 2 * gj) : Op::zero();
+  }
+  if constexpr (KIND == CROSSED) {
+    for (int s = tid; s < (TX + 1) * (TY + 1); s += TX * TY) {
+      int li = s % (TX + 1), lj = s / (TX + 1);
+      int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+      bool in = gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+      sc[lj][li] = in ? op.load(g.nv + gj * g.nx + gi, 2 * gi + 1, 2 * gj + 1) : Op::zero();
+    }
+  }
+  __syncthreads();
+  for (int s = tid; s < (TX + 1) * (TY + 1); s += TX * TY) {
+    int li = s % (TX + 1), lj = s / (TX + 1);
+    int ci = i0 - 1 + li, cj = j0 - 1 + lj;
+    bool valid = ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny;
+    V v00 = sv[lj][li], v10 = sv[lj][li + 1], v01 = sv[lj + 1][li], v11 = sv[lj + 1][li + 1];
+    int cell = cj * g.nx + ci;
+    if constexpr (KIND == CROSSED) {
+      V c = sc[lj][li];
+      se[lj][li][0] = op.template element<0>(valid, cell, cj, v00, v10, c);
+      se[lj][li][1] = op.template element<1>(valid, cell, cj, v10, v11, c);
+      se[lj][li][2] = op.template element<2>(valid, cell, cj, v11, v01, c);
+      se[lj][li][3] = op.template element<3>(valid, cell, cj, v01, v00, c);
+    } else {
+      se[lj][li][0] = op.template element<0>(valid, cell, cj, v00, v10, v11);
+      se[lj][li][1] = op.template element<1>(valid, cell, cj, v00, v11, v01);
+    }
+  }
+  __syncthreads();
+
+  constexpr int NRA = Op::NR > 0 ? Op::NR : 1;
+  double red[NRA];
+#pragma unroll
+  for (int q = 0; q < NRA; ++q) red[q] = Op::RED_MAX ? -INFINITY : 0.0;
+
+  const int i = i0 + tx, j = j0 + ty;
+  if (i <= g.nx && j <= g.ny) {
+    typename Op::Acc a = Op::acc0();
+    if constexpr (KIND == CROSSED) {
+      op.template add<0, 0>(a, se[ty + 1][tx + 1][0]);  // cell (i, j): vertex is v00
+      op.template add<3, 1>(a, se[ty + 1][tx + 1][3]);
+      op.template add<0, 1>(a, se[ty + 1][tx][0]);      // cell (i-1, j): v10
+      op.template add<1, 0>(a, se[ty + 1][tx][1]);
+      op.template add<1, 1>(a, se[ty][tx][1]);          // cell (i-1, j-1): v11
+      op.template add<2, 0>(a, se[ty][tx][2]);
+      op.template add<2, 1>(a, se[ty][tx + 1][2]);      // cell (i, j-1): v01
+      op.template add<3, 0>(a, se[ty][tx + 1][3]);
+    } else {
+      op.template add<0, 0>(a, se[ty + 1][tx + 1][0]);  // cell (i, j): v00
+      op.template add<1, 0>(a, se[ty + 1][tx + 1][1]);
+      op.template add<0, 1>(a, se[ty + 1][tx][0]);      // cell (i-1, j): v10
+      op.template add<0, 2>(a, se[ty][tx][0]);          // cell (i-1, j-1): v11
+      op.template add<1, 1>(a, se[ty][tx][1]);
+      op.template add<1, 2>(a, se[ty][tx + 1][1]);      // cell (i, j-1): v01
+    }
+    op.store(j * (g.nx + 1) + i, 2 * i, 2 * j, sv[ty + 1][tx + 1], a, red);
+  }
+  if constexpr (KIND == CROSSED) {
+    if (i < g.nx && j < g.ny) {
+      typename Op::Acc a = Op::acc0();
+      op.template add<0, 2>(a, se[ty + 1][tx + 1][0]);
+      op.template add<1, 2>(a, se[ty + 1][tx + 1][1]);
+      op.template add<2, 2>(a, se[ty + 1][tx + 1][2]);
+      op.template add<3, 2>(a, se[ty + 1][tx + 1][3]);
+      op.store(g.nv + j * g.nx + i, 2 * i + 1, 2 * j + 1, sc[ty + 1][tx + 1], a, red);
+    }
+  }
+  if constexpr (Op::NR > 0) block_reduce_finalize<Op::NR, Op::RED_MAX>(red, op.args.slot);
+}
+
+// ----------------------------------------------------------------------------------------------
+// elasticity operator K(alpha) (2 dofs per node, interleaved)
+// ----------------------------------------------------------------------------------------------
+// COEF_ALPHA: abar_T from the three nodal damage values; COEF_ELEM: abar_T read per element.
+enum { COEF_ALPHA = 0, COEF_ELEM = 1 };
+
+template <class T>
+struct ElasticArgs {
+  const T* x;         // input displacement (2n)
+  const T* alpha;     // COEF_ALPHA: nodal damage (n)
+  const T* coef;      // COEF_ELEM: abar per element
+  const double* eig;  // EIGEN: eps0 = beta T per (cell row, element)
+  const T* b;         // M_RESB, M_CHEB right-hand side
+  const T* d;         // M_CHEB previous update
+  const T* dinv;      // M_CHEB inverse diagonal (2n)
+  T cd, cr;           // M_CHEB coefficients
+  T* y;               // output (2n); M_CHEB: new x
+  T* dout;            // M_CHEB: new d
+  RedSlot slot;
+};
+
+template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT>
+struct ElasticOp {
+  static constexpr int KIND = KIND_;
+  static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
+  static constexpr bool RED_MAX = false;
+  struct V {
+    T ux, uy, a;
+  };
+  struct R {
+    T sxx, syy, sxy;
+  };
+  struct Acc {
+    T ax, bx, ay, by;
+  };
+  Grid g;
+  Mat m;
+  ElasticArgs<T> args;
+
+  __device__ static V zero() { return V{T(0), T(0), T(0)}; }
+  __device__ static Acc acc0() { return Acc{T(0), T(0), T(0), T(0)}; }
+
+  __device__ V load(int node, int X2, int Y2) const {
+    V v;
+    v.ux = args.x[2 * node];
+    v.uy = args.x[2 * node + 1];
+    if (MODE != M_APPLY && MODE != M_RESID) {
+      if (is_fixed(g, X2, Y2, 0)) v.ux = T(0);
+      if (is_fixed(g, X2, Y2, 1)) v.uy = T(0);
+    }
+    v.a = COEF == COEF_ALPHA ? args.alpha[node] : T(0);
+    return v;
+  }
+
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
+    if (!valid) return R{T(0), T(0), T(0)};
+    constexpr int NE = elems_per_cell(KIND);
+    T w;
+    if (COEF == COEF_ALPHA)
+      w = abar3<T>(n0.a, n1.a, n2.a, T(m.k_ell)) * T(g.area);
+    else
+      w = args.coef[cell * NE + t] * T(g.area);
+    T ihx = T(g.ihx), ihy = T(g.ihy);
+    T sx = T(gx(KIND, t, 0)) * n0.ux + T(gx(KIND, t, 1)) * n1.ux + T(gx(KIND, t, 2)) * n2.ux;
+    T sy = T(gy(KIND, t, 0)) * n0.uy + T(gy(KIND, t, 1)) * n1.uy + T(gy(KIND, t, 2)) * n2.uy;
+    T s1 = T(gy(KIND, t, 0)) * n0.ux + T(gy(KIND, t, 1)) * n1.ux + T(gy(KIND, t, 2)) * n2.ux;
+    T s2 = T(gx(KIND, t, 0)) * n0.uy + T(gx(KIND, t, 1)) * n1.uy + T(gx(KIND, t, 2)) * n2.uy;
+    T exx = ihx * sx, eyy = ihy * sy, gxy = ihy * s1 + ihx * s2;
+    if (EIGEN) {
+      T e0 = T(args.eig[cj * NE + t]);
+      exx -= e0;
+      eyy -= e0;
+    }
+    T lam = T(m.lam), l2m = T(m.lam2mu), mu = T(m.mu);
+    return R{w * (l2m * exx + lam * eyy), w * (lam * exx + l2m * eyy), w * mu * gxy};
+  }
+
+  template <int t, int k>
+  __device__ void add(Acc& a, const R& r) const {
+    constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
+    if (cx != 0) {
+      a.ax += T(cx) * r.sxx;
+      a.ay += T(cx) * r.sxy;
+    }
+    if (cy != 0) {
+      a.bx += T(cy) * r.sxy;
+      a.by += T(cy) * r.syy;
+    }
+  }
+
+  __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
+                        double (&red)[NR > 0 ? NR : 1]) const {
+    T fx = T(g.ihx) * a.ax + T(g.ihy) * a.bx;
+    T fy = T(g.ihx) * a.ay + T(g.ihy) * a.by;
+    bool f0 = false, f1 = false;
+    if (MODE != M_APPLY) {
+      f0 = is_fixed(g, X2, Y2, 0);
+      f1 = is_fixed(g, X2, Y2, 1);
+    }
+    if (MODE == M_APPLY || MODE == M_MASKED) {
+      T yx = f0 ? T(0) : fx, yy = f1 ? T(0) : fy;
+      args.y[2 * node] = yx;
+      args.y[2 * node + 1] = yy;
+      if (DOT) red[0] += double(own.ux) * double(yx) + double(own.uy) * double(yy);
+    } else if (MODE == M_RESB) {
+      T rx = f0 ? T(0) : args.b[2 * node] - fx, ry = f1 ? T(0) : args.b[2 * node + 1] - fy;
+      args.y[2 * node] = rx;
+      args.y[2 * node + 1] = ry;
+      if (DOT) red[0] += double(rx) * double(rx) + double(ry) * double(ry);
+    } else if (MODE == M_RESID) {
+      T rx = f0 ? T(0) : -fx, ry = f1 ? T(0) : -fy;
+      args.y[2 * node] = rx;
+      args.y[2 * node + 1] = ry;
+      red[0] += double(rx) * double(rx) + double(ry) * double(ry);
+    } else if (MODE == M_CHEB) {
+      T rx = args.b[2 * node] - fx, ry = args.b[2 * node + 1] - fy;
+      T px = args.d ? args.d[2 * node] : T(0), py = args.d ? args.d[2 * node + 1] : T(0);
+      T dx = f0 ? T(0) : args.cd * px + args.cr * args.dinv[2 * node] * rx;
+      T dy = f1 ? T(0) : args.cd * py + args.cr * args.dinv[2 * node + 1] * ry;
+      args.dout[2 * node] = dx;
+      args.dout[2 * node + 1] = dy;
+      args.y[2 * node] = own.ux + dx;
+      args.y[2 * node + 1] = own.uy + dy;
+    }
+  }
+};
+
+// ----------------------------------------------------------------------------------------------
+// damage Hessian H(q) (1 dof per node); gradient / MCP residual / active set in FP64
+// ----------------------------------------------------------------------------------------------
+template <class T>
+struct DamageArgs {
+  const T* x;           // input field (n)
+  const T* w;           // per-element mass weight; M_GRAD/M_TRIAL: q_T (weight q + c2)
+  const uint8_t* excl;  // M_MASKED/M_RESB/M_CHEB: 1 = excluded (active or fixed) node
+  const T* b;           // M_RESB, M_CHEB
+  const T* d;           // M_CHEB previous update; M_TRIAL direction
+  const T* dinv;        // M_CHEB
+  const double* lo;     // M_GRAD/M_TRIAL: lower bound alpha_prev
+  T cd, cr;             // M_CHEB coefficients; M_TRIAL: cd = step mu
+  double zeta;
+  T* y;                 // output: M_APPLY..M_CHEB result; M_GRAD/M_TRIAL: F
+  T* dout;              // M_CHEB new d; M_GRAD/M_TRIAL: Phi
+  T* rhs;               // M_GRAD/M_TRIAL: -F on the inactive set, 0 elsewhere
+  T* xt;                // M_TRIAL: trial point
+  uint8_t* act;         // M_GRAD/M_TRIAL: active flags written
+  RedSlot slot;
+};
+
+template <class T, int KIND_, int MODE, bool DOT>
+struct DamageOp {
+  static constexpr int KIND = KIND_;
+  static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
+  static constexpr bool RED_MAX = false;
+  struct V {
+    T p;
+  };
+  struct R {
+    T P, M, X, Y;
+  };
+  struct Acc {
+    T P, M, X, Y;
+  };
+  Grid g;
+  Mat m;
+  DamageArgs<T> args;
+
+  __device__ static V zero() { return V{T(0)}; }
+  __device__ static Acc acc0() { return Acc{T(0), T(0), T(0), T(0)}; }
+
+  __device__ double upper(int X2, int Y2, double l) const {
+    return is_fixed(g, X2, Y2, 2) ? l : 1.0;
+  }
+
+  __device__ V load(int node, int X2, int Y2) const {
+    V v;
+    if (MODE == M_TRIAL) {
+      double l = args.lo[node], h = upper(X2, Y2, l);
+      double z = double(args.x[node]) + double(args.cd) * double(args.d[node]);
+      v.p = T(fmin(fmax(z, l), h));
+    } else {
+      v.p = args.x[node];
+      if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl[node]) v.p = T(0);
+    }
+    return v;
+  }
+
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
+    if (!valid) return R{T(0), T(0), T(0), T(0)};
+    constexpr int NE = elems_per_cell(KIND);
+    T area = T(g.area);
+    T wt = args.w[cell * NE + t];
+    T qT = wt;
+    if (MODE == M_GRAD || MODE == M_TRIAL) wt = wt + T(m.c2);
+    T me = wt * area * T(1.0 / 12.0);
+    T S = n0.p + n1.p + n2.p;
+    T gpx = T(g.ihx) * (T(gx(KIND, t, 0)) * n0.p + T(gx(KIND, t, 1)) * n1.p + T(gx(KIND, t, 2)) * n2.p);
+    T gpy = T(g.ihy) * (T(gy(KIND, t, 0)) * n0.p + T(gy(KIND, t, 1)) * n1.p + T(gy(KIND, t, 2)) * n2.p);
+    T c1a = T(m.c1) * area;
+    T P = me * S;
+    if (MODE == M_GRAD || MODE == M_TRIAL) P += (T(m.c3) - qT) * area * T(1.0 / 3.0);
+    return R{P, me, c1a * T(g.ihx) * gpx, c1a * T(g.ihy) * gpy};
+  }
+
+  template <int t, int k>
+  __device__ void add(Acc& a, const R& r) const {
+    constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
+    a.P += r.P;
+    a.M += r.M;
+    if (cx != 0) a.X += T(cx) * r.X;
+    if (cy != 0) a.Y += T(cy) * r.Y;
+  }
+
+  __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
+                        double (&red)[NR > 0 ? NR : 1]) const {
+    T f = a.P + a.M * own.p + a.X + a.Y;
+    if (MODE == M_APPLY) {
+      args.y[node] = f;
+      if (DOT) red[0] += double(own.p) * double(f);
+    } else if (MODE == M_MASKED) {
+      T v = args.excl[node] ? T(0) : f;
+      args.y[node] = v;
+      if (DOT) red[0] += double(own.p) * double(v);
+    } else if (MODE == M_RESB) {
+      T r = args.excl[node] ? T(0) : args.b[node] - f;
+      args.y[node] = r;
+      if (DOT) red[0] += double(r) * double(r);
+    } else if (MODE == M_CHEB) {
+      T dp = args.d ? args.d[node] : T(0);
+      T dn = args.excl[node] ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
+      args.dout[node] = dn;
+      args.y[node] = own.p + dn;
+    } else {  // M_GRAD / M_TRIAL (T = double)
+      double xv = double(own.p), F = double(f);
+      double l = args.lo[node], h = upper(X2, Y2, l);
+      double ph = mcp_phi(xv, F, l, h);
+      bool active = (h - l <= args.zeta) || (xv <= l + args.zeta && F > 0.0) || (xv >= h - args.zeta && F < 0.0);
+      args.y[node] = T(F);
+      args.dout[node] = T(ph);
+      args.rhs[node] = active ? T(0) : T(-F);
+      args.act[node] = active ? 1 : 0;
+      if (MODE == M_TRIAL) args.xt[node] = own.p;
+      red[0] += ph * ph;
+      red[1] += active ? 0.0 : F * F;
+    }
+  }
+};
+
+}  // namespace pf

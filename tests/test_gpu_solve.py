@@ -1,0 +1,139 @@
+"""GPU parity of the subproblem solves and of whole load steps (Algorithms 1, 2 and 4) against
+the oracle: fields within 1e-6 relative in the max norm, energies within 1e-8 relative (FP64);
+the mixed-precision path within 1e-6 relative energy."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import am, fe
+from oracle.problem import Problem
+
+from .gpu_util import need_gpu, rel_max, tight_opts
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields_close(g, p, tol=1e-6):
+    u, a, ap = g.get_fields()
+    assert np.abs(a - p.alpha).max() <= tol, np.abs(a - p.alpha).max()
+    assert rel_max(u, p.u) <= tol, rel_max(u, p.u)
+    assert np.abs(ap - p.alpha_prev).max() <= tol
+
+
+@pytest.mark.parametrize("w", [W.notched_square(n=32), W.bar(nx=64, ny=8),
+                               W.thermal_shock(nx=64, ny=16)], ids=["notched", "bar", "thermal"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_u_solve(w, precision):
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    p = Problem(w)
+    rng = np.random.default_rng(3)
+    alpha = rng.uniform(0, 0.9, p.mesh.n_nodes)
+    alpha[p.a_fixed] = p.a_value[p.a_fixed]
+    t, dT = w.loads[10]
+    g = S.Sim(w)
+    g.set_fields(alpha=alpha)
+    g.set_load(t, dT)
+    p.alpha = alpha
+    p.lift(t)
+    g.u_solve(tight_opts(S, precision=precision))
+    uref = am.solve_u(p, alpha, dT)
+    u, _, _ = g.get_fields()
+    assert rel_max(u, uref) <= 1e-9
+
+
+@pytest.mark.parametrize("model", ["AT1", "AT2"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_alpha_solve(model, precision):
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    w = W.notched_square(n=32, model=model)
+    p = Problem(w)
+    rng = np.random.default_rng(4)
+    G = np.array([[0.6, 0.2], [0.1, 1.4]]) * (4.0 if model == "AT1" else 1.0)
+    u = p.mesh.xy @ G.T + 0.05 * rng.normal(size=(p.mesh.n_nodes, 2))
+    ap = np.where(p.alpha == 1.0, 1.0, rng.uniform(0, 0.2, p.mesh.n_nodes))
+    g = S.Sim(w)
+    g.set_fields(u=u, alpha=ap, alpha_prev=ap)
+    g.set_load(0.0, 0.0)
+    rep = g.alpha_solve(tight_opts(S, precision=precision))
+    p.u, p.alpha, p.alpha_prev = u, ap.copy(), ap.copy()
+    aref, info = am.solve_alpha(p, u, ap.copy(), 0.0)
+    _, a, _ = g.get_fields()
+    assert np.abs(a - aref).max() <= 1e-8
+    assert 0 < np.sum((aref > ap + 1e-12)) < aref.size  # a genuine box-constrained solve
+    assert rep["rs_iters"] >= 1
+
+
+def _run_steps(w, steps, omega, precision="fp64", **kw):
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    g = S.Sim(w)
+    p = Problem(w)
+    opts = tight_opts(S, omega=omega, precision=precision, **kw)
+    reps = []
+    for (t, dT) in steps:
+        rep = g.load_step(t, dT, opts)
+        r = am.load_step(p, t, dT, omega=omega, tol=1e-10)
+        reps.append((rep, r))
+    return g, p, reps
+
+
+def test_notched_oram_load_steps():
+    w = W.notched_square(n=32, n_steps=10, t_max=1.0)
+    g, p, reps = _run_steps(w, w.loads[:7], omega=1.5)
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+        assert rep["status"] == 0
+    _fields_close(g, p)
+    assert p.alpha[p.alpha_prev < 1].max() > 0.1  # damage has developed beyond the notch
+
+
+def test_bar_am_through_nucleation():
+    """Bar (Section 4.2) with the symmetry-breaking seed column at x = L/2 (design reading of
+    the bifurcation at nucleation); AM (omega = 1)."""
+    w = W.bar(nx=64, ny=8, n_steps=20, seed_column=True)
+    g, p, reps = _run_steps(w, w.loads[11:16], omega=1.0)
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+    _fields_close(g, p)
+    assert p.alpha.max() > 0.9
+
+
+def test_thermal_onset():
+    w = W.thermal_shock(nx=64, ny=16, n_steps=40)
+    g, p, reps = _run_steps(w, w.loads[8:12], omega=1.6)
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+    _fields_close(g, p)
+
+
+def test_at2_notched():
+    w = W.notched_square(n=16, n_steps=10, t_max=1.0, model="AT2")
+    g, p, reps = _run_steps(w, w.loads[:5], omega=1.3)
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+    _fields_close(g, p)
+
+
+def test_mixed_precision_energy_error():
+    w = W.notched_square(n=32, n_steps=10, t_max=1.0)
+    g, p, reps = _run_steps(w, w.loads[:6], omega=1.5, precision="mixed", inner_rtol=1e-4)
+    for rep, r in reps:
+        assert abs(rep["energy"][2] - r["energy"][2]) <= 1e-6 * abs(r["energy"][2])
+    _fields_close(g, p, tol=1e-5)
+
+
+def test_single_level_and_jacobi_paths():
+    """Odd mesh sizes have no coarse level: the solver runs Chebyshev-preconditioned CG."""
+    w = W.notched_square(n=18, n_steps=10, t_max=1.0)
+    w.nx = w.ny = 17
+    w.alpha_boxes = [(0, 17, 15, 19, 1.0)]
+    g, p, reps = _run_steps(w, w.loads[:4], omega=1.5)
+    assert g.levels == 1
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+    _fields_close(g, p)
