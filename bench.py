@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Benchmark: quasi-static load steps per second of the single-edge notched square on a
+1024 x 1024 crossed P1 mesh (6.3M dofs, AT1, ell = 4h, ORAM omega = 1.5, 50 load steps to
+t = 0.6), mixed precision (FP32 inner solves, FP64 residuals and decisions) against the plain
+FP64 GPU path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one load step (Algorithm 2 to convergence).  The W warm-up steps are the first W
+steps of the schedule; the K timed steps are the next K (capped at the end of the schedule).
+Replicas only: under torchrun every rank solves its own copy (no collective on the data path);
+the time is the max over ranks and the value counts the steps of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "load steps/s at 1024^2 mesh (notched square, ORAM omega=1.5), mixed vs FP64 GPU"
+UNIT = "load_steps/s"
+L2_BYTES = 126.5e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=47)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="-1: same as --steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quiet", action="store_true")
+    return ap.parse_args()
+
+
+def log(args, *a):
+    if not args.quiet:
+        print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        smax = max((num(r[1]) or 0) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        loaded = [s for s in sm if s >= 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on a bounded sample
+# ---------------------------------------------------------------------------------------------
+ORACLE_SAMPLE = r"""
+import sys, time, json
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+from oracle import am
+from oracle.problem import Problem
+out = {}
+for n in (128, 256):
+    w = W.notched_square(n=n)
+    p = Problem(w)
+    am.begin_step(p, *w.loads[int(sys.argv[2])])
+    t0 = time.perf_counter()
+    am.oram_iteration(p, w.omega, 0.0)
+    out[n] = time.perf_counter() - t0
+print(json.dumps(out))
+"""
+
+
+def oracle_iteration_seconds(target_n: int, step_index: int):
+    """Seconds per ORAM iteration of the oracle at target_n^2, extrapolated with the size
+    exponent fitted between one iteration at 128^2 and one at 256^2 (single thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE, ROOT, str(step_index)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    t = {int(k): v for k, v in json.loads(r.stdout.strip().splitlines()[-1]).items()}
+    p = math.log(t[256] / t[128]) / math.log(4.0)  # node count grows 4x per refinement
+    ratio = (target_n / 256.0) ** 2
+    return t[256] * ratio ** p, t, p
+
+
+def iterations_lower_bound(omega: float, tol: float) -> int:
+    """ORAM iterations of a load step in which the damage does not move: the over-relaxed
+    u-update contracts the error by |1 - omega| per iteration (Section 2.1)."""
+    return int(math.ceil(math.log(tol) / math.log(abs(1.0 - omega)))) + 1
+
+
+def cpu_baseline_record(size: int, omega: float, tol: float, step_index: int):
+    it_s, t, p = oracle_iteration_seconds(size, step_index)
+    n_it = iterations_lower_bound(omega, tol)
+    return {"value": 1.0 / (it_s * n_it), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one ORAM iteration of the FP64 oracle (sparse LU solves) at 128^2 "
+                       f"({t[128]:.1f}s) and 256^2 ({t[256]:.1f}s), load step {step_index + 1}; "
+                       f"time per iteration extrapolated to {size}^2 with the fitted size exponent "
+                       f"{p:.2f} ({it_s:.0f}s), times {n_it} iterations per load step (the ORAM "
+                       f"contraction bound |1-omega|^k <= tol of a step without damage growth, a "
+                       f"lower bound, so the baseline is optimistic); extrapolated")}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the oracle timed on the host cores
+# ---------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import workloads as W
+    from oracle import am
+    from oracle.problem import Problem
+
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    w = W.notched_square(n=args.size)
+    t_big, t, p = oracle_iteration_seconds(args.size, args.warmup)
+    n_small = 128
+    ws = W.notched_square(n=n_small)
+    prob = Problem(ws)
+    scale = ((args.size / n_small) ** 2) ** p
+    n_it = iterations_lower_bound(w.omega, 1e-6)
+    nsteps = min(args.steps, len(w.loads) - args.warmup)
+    for k in range(args.warmup):  # warm-up samples
+        am.begin_step(prob, *ws.loads[k])
+        am.oram_iteration(prob, ws.omega, 0.0)
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + nsteps):
+        am.begin_step(prob, *ws.loads[k])
+        am.oram_iteration(prob, ws.omega, 0.0)
+    el = time.perf_counter() - t0
+    per_it = el / nsteps * scale
+    value = 1.0 / (per_it * n_it)
+    sample = (f"each step: one ORAM iteration of the FP64 oracle at {n_small}^2 on load step k, "
+              f"scaled to {args.size}^2 by the size exponent {p:.2f} fitted from 128^2/256^2 "
+              f"iterations, times {n_it} iterations per load step (lower bound); extrapolated")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": nsteps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"notched_square_{args.size}_crossed_AT1_ORAM_omega1.5",
+                       "mesh": f"{args.size}x{args.size} crossed P1", "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def aggregate_max(value: float) -> float:
+    """Max of a per-rank scalar over all ranks (1 rank: identity)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def traffic_from_profiles(kclass: str):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 2 and parts[0] == kclass and not line.startswith("#"):
+                try:
+                    return float(parts[1])
+                except ValueError:
+                    return None
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1511_08463_gb300 import _build
+
+    if rank == 0:
+        _build.build()
+    barrier()
+    import workloads as W
+    from paper_1511_08463_gb300 import binding as B
+    from paper_1511_08463_gb300 import sim as S
+
+    lib = B.load()
+    w = W.notched_square(n=args.size)
+    nsched = len(w.loads)
+    W0 = min(args.warmup, nsched - 1)
+    K = max(1, min(args.steps, nsched - W0))
+    ctx = S.Context(local)
+    sim = S.Sim(w, ctx)
+    opts = S.make_opts(algo="ORAM", omega=w.omega, precision=args.precision)
+    log(args, f"[rank {rank}] nodes {sim.n_nodes} levels {sim.levels} workspace "
+              f"{sim.workspace_bytes / 1e9:.2f} GB; warm-up {W0} steps")
+    # warm-up: the first W0 steps; the last one is profiled for every kernel class
+    for k in range(W0):
+        if k == W0 - 1:
+            lib.pf_prof_reset()
+            lib.pf_prof_enable(1, -1)
+        sim.load_step(*w.loads[k], opts, allow_notconv=True)
+    lib.pf_prof_enable(0, -1)
+    warm_tab = B.prof_table()
+    dominant = max(warm_tab.items(), key=lambda kv: kv[1]["ms"])[0] if warm_tab else None
+    dom_id = warm_tab[dominant]["id"] if dominant else -1
+    snap = sim.get_fields()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident state) ------------------------------------------------
+    lib.pf_prof_reset()
+    lib.pf_prof_enable(1, dom_id)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = lib.pf_launch_count()
+    ev0.record()
+    reps = []
+    for k in range(W0, W0 + K):
+        reps.append(sim.load_step(*w.loads[k], opts, allow_notconv=True))
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = lib.pf_launch_count() - launches0
+    clk = clocks.stop()
+    lib.pf_prof_enable(0, -1)
+    tab = B.prof_table()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed_max = aggregate_max(elapsed)
+    value = K * world / elapsed_max
+    final_fields = sim.get_fields()
+
+    # roofline of the dominant kernel class, timed live on its launching stream
+    import json as _json
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = _json.load(fh)
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "of measured" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or 6800.0
+    roof = None
+    if dominant and dominant in tab and tab[dominant]["timed"]:
+        d = tab[dominant]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        per_launch = d["bytes"] / d["timed"]
+        traffic = traffic_from_profiles(dominant)
+        bound = "hbm"
+        roof = {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src,
+                "traffic": traffic, "algorithmic_bytes_per_launch": per_launch,
+                "avg_launch_us": d["ms"] * 1e3 / d["timed"], "launches": d["timed"],
+                "share_of_timed_region": d["ms"] / 1e3 / elapsed}
+
+    # ---- end to end through host buffers ------------------------------------------------------
+    KE = K if args.e2e_steps < 0 else max(1, min(args.e2e_steps, K))
+    n = sim.n_nodes
+    hu = torch.empty((n, 2), dtype=torch.float64, pin_memory=True)
+    ha = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hp = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hu.numpy()[:] = snap[0]
+    ha.numpy()[:] = snap[1]
+    hp.numpy()[:] = snap[2]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_ev0 = torch.cuda.Event(enable_timing=True)
+    e2e_ev1 = torch.cuda.Event(enable_timing=True)
+    e2e_ev0.record()
+    for k in range(W0, W0 + KE):
+        B.check(lib.pf_set_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
+        sim.load_step(*w.loads[k], opts, allow_notconv=True)
+        B.check(lib.pf_get_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
+    e2e_ev1.record()
+    torch.cuda.synchronize()
+    e2e_el = aggregate_max(e2e_ev0.elapsed_time(e2e_ev1) / 1e3)
+    e2e_value = KE * world / e2e_el
+    same = bool(np.array_equal(hu.numpy(), final_fields[0])) if KE == K else None
+
+    # ---- FP64 GPU path on the first steps of the same window ------------------------------
+    fp = None
+    KF = min(args.fp64_steps, K)
+    if KF > 0:
+        sim.set_fields(*snap)
+        o64 = S.make_opts(algo="ORAM", omega=w.omega, precision="fp64")
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        reps64 = [sim.load_step(*w.loads[k], o64, allow_notconv=True) for k in range(W0, W0 + KF)]
+        f1.record()
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1e3
+        tmix = sum(r["seconds"] for r in reps[:KF])
+        err = max(abs(a["energy"][2] - b["energy"][2]) / max(abs(b["energy"][2]), 1e-300)
+                  for a, b in zip(reps[:KF], reps64))
+        fp = {"steps": f"{W0 + 1}-{W0 + KF}", "fp64_steps_per_s": KF / t64,
+              "mixed_steps_per_s": KF / tmix, "mixed_speedup": t64 / tmix,
+              "max_rel_energy_diff_mixed_vs_fp64": err}
+
+    # ---- CPU baseline -------------------------------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_record(args.size, w.omega, 1e-6, W0)
+        except Exception as e:  # report, never fake
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {e!s}"[:300]}
+
+    if rank == 0:
+        am_its = [r["am_iters"] for r in reps]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W0, "ms_per_step": elapsed_max / K * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {
+                "workload": f"notched_square_{args.size}_crossed_AT1_ORAM_omega1.5",
+                "mesh": f"{args.size}x{args.size} crossed P1", "dofs": 3 * sim.n_nodes,
+                "load_steps": f"{W0 + 1}-{W0 + K} of {nsched} (t up to {w.loads[-1][0]})",
+                "precision": args.precision, "parallelism": f"replicas x{world}",
+                "l2": f"inputs larger than L2: resident state + work buffers "
+                      f"{sim.workspace_bytes / 1e9:.2f} GB per replica"},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
+                    "d2h_bytes_per_step": 32 * n, "steps": KE,
+                    "same_state_as_device_run": same},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "fp64_window": fp,
+            "solver": {"am_iters_per_step": am_its,
+                       "cg_u": sum(r["cg_iters_u"] for r in reps),
+                       "cg_alpha": sum(r["cg_iters_alpha"] for r in reps),
+                       "rs_iters": sum(r["rs_iters"] for r in reps),
+                       "not_converged_steps": sum(1 for r in reps if r["status"] != 0),
+                       "final_energy": reps[-1]["energy"]},
+            "kernel_classes_warmup_step": {k: {"ms": round(v["ms"], 3),
+                                               "launches": v["launches"]}
+                                           for k, v in sorted(warm_tab.items(),
+                                                              key=lambda kv: -kv[1]["ms"])[:12]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

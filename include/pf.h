@@ -241,6 +241,23 @@ pf_status pf_op_alpha_solve(pf_sim* sim, const pf_solver_opts* o, void* stream,
  * E_alpha) at the resident state and current load.  Synchronous. */
 pf_status pf_op_full_residual(pf_sim* sim, double* phi_norm, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Launch accounting and kernel timing (tracing support; process-wide, not thread-safe).
+ * Every kernel the library launches is counted.  With timing enabled, each launch of the
+ * selected kernel class (-1 = every class) is bracketed by two CUDA events recorded on the
+ * launching stream; the measured time and the launch's algorithmic bytes (compulsory reads and
+ * writes of the operator on its grid) are accumulated per class.
+ * ------------------------------------------------------------------------------------------ */
+pf_status pf_prof_enable(int on, int kernel_class);
+pf_status pf_prof_reset(void);
+int64_t pf_launch_count(void);
+int pf_prof_class_count(void);
+/* name: static string valid until the next call on this thread; launches: all launches of the
+ * class since the last reset; timed: launches that were timed; ms: summed event time; bytes:
+ * summed algorithmic bytes of the timed launches.  PF_EINVAL for an unknown class. */
+pf_status pf_prof_get(int kernel_class, const char** name, int64_t* launches, int64_t* timed,
+                      double* ms, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,13 @@ _SIGS = {
     "pf_op_alpha_solve": (C.c_int, [_VP, C.POINTER(pf_solver_opts), _VP,
                                     C.POINTER(pf_step_report)]),
     "pf_op_full_residual": (C.c_int, [_VP, C.POINTER(C.c_double), _VP]),
+    "pf_prof_enable": (C.c_int, [C.c_int, C.c_int]),
+    "pf_prof_reset": (C.c_int, []),
+    "pf_launch_count": (C.c_int64, []),
+    "pf_prof_class_count": (C.c_int, []),
+    "pf_prof_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -131,3 +138,16 @@ def check(status: int, allow=(PF_OK,)):
     if status not in allow:
         raise PFError(status, load().pf_last_error().decode())
     return status
+
+
+def prof_table():
+    """Per kernel class: name -> dict(launches, timed, ms, bytes)."""
+    lib = load()
+    out = {}
+    for k in range(lib.pf_prof_class_count()):
+        nm, la, ti, ms, by = C.c_char_p(), C.c_int64(), C.c_int64(), C.c_double(), C.c_double()
+        check(lib.pf_prof_get(k, C.byref(nm), C.byref(la), C.byref(ti), C.byref(ms), C.byref(by)))
+        if la.value or ti.value:
+            out[nm.value.decode()] = dict(id=k, launches=la.value, timed=ti.value, ms=ms.value,
+                                          bytes=by.value)
+    return out

@@ -1,5 +1,6 @@
 // Host-side launchers of the libpf kernels (definitions in ops_*.cu and kernels_misc.cu).
 #pragma once
+#include "prof.hpp"
 #include "stencil.cuh"
 
 namespace pf {

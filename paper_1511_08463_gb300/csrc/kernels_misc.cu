@@ -26,7 +26,7 @@ __global__ void k_fill(T* y, T v, size_t n) {
 }
 template <class T>
 void vec_fill(cudaStream_t s, T* y, T v, size_t n) {
-  k_fill<<<nblocks(n), RED_THREADS, 0, s>>>(y, v, n);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_fill<<<nblocks(n), RED_THREADS, 0, s>>>(y, v, n));
 }
 template void vec_fill<double>(cudaStream_t, double*, double, size_t);
 template void vec_fill<float>(cudaStream_t, float*, float, size_t);
@@ -38,7 +38,7 @@ __global__ void k_convert(TO* y, const TI* x, size_t n) {
 }
 template <class TO, class TI>
 void vec_convert(cudaStream_t s, TO* y, const TI* x, size_t n) {
-  k_convert<TO, TI><<<nblocks(n), RED_THREADS, 0, s>>>(y, x, n);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_convert<TO, TI><<<nblocks(n), RED_THREADS, 0, s>>>(y, x, n));
 }
 template void vec_convert<float, double>(cudaStream_t, float*, const double*, size_t);
 template void vec_convert<double, float>(cudaStream_t, double*, const float*, size_t);
@@ -49,7 +49,7 @@ __global__ void k_add_f32_to_f64(double* x, const float* d, size_t n) {
   if (i < n) x[i] += (double)d[i];
 }
 void vec_add_f32_to_f64(cudaStream_t s, double* x, const float* d, size_t n) {
-  k_add_f32_to_f64<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_add_f32_to_f64<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n));
 }
 
 template <class T>
@@ -59,7 +59,7 @@ __global__ void k_add(T* x, const T* d, size_t n) {
 }
 template <class T>
 void vec_add(cudaStream_t s, T* x, const T* d, size_t n) {
-  k_add<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_add<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n));
 }
 template void vec_add<double>(cudaStream_t, double*, const double*, size_t);
 template void vec_add<float>(cudaStream_t, float*, const float*, size_t);
@@ -71,7 +71,7 @@ __global__ void k_mul(T* z, const T* a, const T* b, size_t n) {
 }
 template <class T>
 void vec_mul(cudaStream_t s, T* z, const T* a, const T* b, size_t n) {
-  k_mul<<<nblocks(n), RED_THREADS, 0, s>>>(z, a, b, n);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_mul<<<nblocks(n), RED_THREADS, 0, s>>>(z, a, b, n));
 }
 template void vec_mul<double>(cudaStream_t, double*, const double*, const double*, size_t);
 template void vec_mul<float>(cudaStream_t, float*, const float*, const float*, size_t);
@@ -86,7 +86,7 @@ __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
 }
 template <class T>
 void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot) {
-  k_dot<<<rblocks(n), RED_THREADS, 0, s>>>(x, y, n, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_dot<<<rblocks(n), RED_THREADS, 0, s>>>(x, y, n, slot));
 }
 template void vec_dot<double>(cudaStream_t, const double*, const double*, size_t, RedSlot);
 template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, RedSlot);
@@ -109,7 +109,7 @@ __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const dou
 template <class T>
 void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
                   const double* pAp, RedSlot slot) {
-  k_cg_xr<<<rblocks(n), RED_THREADS, 0, s>>>(x, r, p, Ap, n, rz, pAp, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_cg_xr<<<rblocks(n), RED_THREADS, 0, s>>>(x, r, p, Ap, n, rz, pAp, slot));
 }
 template void cg_update_xr<double>(cudaStream_t, double*, double*, const double*, const double*,
                                    size_t, const double*, const double*, RedSlot);
@@ -130,7 +130,7 @@ __global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const d
 template <class T>
 void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
                  const double* rz_old) {
-  k_cg_p<<<nblocks(n), RED_THREADS, 0, s>>>(p, z, n, rz_new, rz_old);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_cg_p<<<nblocks(n), RED_THREADS, 0, s>>>(p, z, n, rz_new, rz_old));
 }
 template void cg_update_p<double>(cudaStream_t, double*, const double*, size_t, const double*,
                                   const double*);
@@ -151,7 +151,7 @@ __global__ void k_relax_u(double* u, const double* xt, double omega, size_t n2, 
   block_reduce_finalize<2, true>(v, slot);
 }
 void relax_u(cudaStream_t s, double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
-  k_relax_u<<<rblocks(n2), RED_THREADS, 0, s>>>(u, xt, omega, n2, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_relax_u<<<rblocks(n2), RED_THREADS, 0, s>>>(u, xt, omega, n2, slot));
 }
 
 __device__ __forceinline__ double upper_of(const Grid& g, int node, double lo) {
@@ -176,7 +176,7 @@ __global__ void k_omega_star(Grid g, const double* alpha, const double* at, cons
 }
 void omega_star(cudaStream_t s, const Grid& g, const double* alpha, const double* at,
                 const double* lo, RedSlot slot) {
-  k_omega_star<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_omega_star<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, slot));
 }
 
 __global__ void k_relax_alpha(Grid g, double* alpha, const double* at, const double* lo, double w,
@@ -194,7 +194,7 @@ __global__ void k_relax_alpha(Grid g, double* alpha, const double* at, const dou
 }
 void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at, const double* lo,
                  double w, float* alpha32, RedSlot slot) {
-  k_relax_alpha<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, w, alpha32, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_relax_alpha<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, w, alpha32, slot));
 }
 
 __global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
@@ -219,8 +219,8 @@ __global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
   }
 }
 void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld) {
-  k_lift<<<nblocks(g.nv), RED_THREADS, 0, s>>>(g, u, t, ld);
-  if (g.npins > 0) k_lift_pins<<<1, 1, 0, s>>>(g, u, t, ld);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_lift<<<nblocks(g.nv), RED_THREADS, 0, s>>>(g, u, t, ld));
+  if (g.npins > 0) PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_lift_pins<<<1, 1, 0, s>>>(g, u, t, ld));
 }
 
 template <class T>
@@ -238,7 +238,7 @@ __global__ void k_mask_fixed(Grid g, T* v, int ncomp) {
 }
 template <class T>
 void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp) {
-  k_mask_fixed<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, v, ncomp);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_mask_fixed<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, v, ncomp));
 }
 template void mask_fixed<double>(cudaStream_t, const Grid&, double*, int);
 template void mask_fixed<float>(cudaStream_t, const Grid&, float*, int);
@@ -278,7 +278,7 @@ __global__ void k_elastic_coef(Grid g, Mat m, const T* alpha, T* coef) {
 }
 template <class T>
 void elastic_coef(cudaStream_t s, const Grid& g, const Mat& m, const T* alpha, T* coef) {
-  k_elastic_coef<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, alpha, coef);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_elastic_coef<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, alpha, coef));
 }
 template void elastic_coef<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void elastic_coef<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -324,7 +324,7 @@ __global__ void k_damage_q(Grid g, Mat m, const double* u, const double* eig, do
 }
 void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
               double* q, double* w64, float* w32) {
-  k_damage_q<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, eig, q, w64, w32);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_damage_q<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, eig, q, w64, w32));
 }
 
 __global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, const double* eig,
@@ -360,7 +360,7 @@ __global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, co
 }
 void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* alpha,
             const double* eig, RedSlot slot) {
-  k_energy<<<rblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, alpha, eig, slot);
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_energy<<<rblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, alpha, eig, slot));
 }
 
 // children of coarse element t of coarse cell (I, J): fine cells and fine element types
@@ -389,7 +389,7 @@ __global__ void k_coarsen(Grid gf, Grid gc, const T* cf, T* cc) {
 }
 template <class T>
 void coarsen_coef(cudaStream_t s, const Grid& gf, const Grid& gc, const T* cf, T* cc) {
-  k_coarsen<<<nblocks(gc.ncell), RED_THREADS, 0, s>>>(gf, gc, cf, cc);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarsen<<<nblocks(gc.ncell), RED_THREADS, 0, s>>>(gf, gc, cf, cc));
 }
 template void coarsen_coef<double>(cudaStream_t, const Grid&, const Grid&, const double*, double*);
 template void coarsen_coef<float>(cudaStream_t, const Grid&, const Grid&, const float*, float*);
@@ -456,7 +456,7 @@ __global__ void k_l1_elastic(Grid g, Mat m, const T* coef, T* dinv) {
 }
 template <class T>
 void l1_dinv_elastic(cudaStream_t s, const Grid& g, const Mat& m, const T* coef, T* dinv) {
-  k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, coef, dinv);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, coef, dinv));
 }
 template void l1_dinv_elastic<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_elastic<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -484,7 +484,7 @@ __global__ void k_l1_damage(Grid g, Mat m, const T* w, T* dinv) {
 }
 template <class T>
 void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* dinv) {
-  k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, w, dinv);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, w, dinv));
 }
 template void l1_dinv_damage<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_damage<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -538,7 +538,7 @@ __global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* 
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
                   const T* rf, T* bc) {
-  k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc);
+  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc));
 }
 template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
                                    double*);
@@ -582,7 +582,7 @@ __global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* x
 template <class T>
 void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
                  const T* xc, T* xf, const uint8_t* excl) {
-  k_prolong<<<nblocks(gf.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, xc, xf, excl);
+  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_prolong<<<nblocks(gf.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, xc, xf, excl));
 }
 template void prolong_add<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
                                   double*, const uint8_t*);
@@ -647,7 +647,7 @@ template <class T>
 void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef, T* A,
                      T* diag0) {
   int nd = g.n * (physics == 0 ? 2 : 1);
-  k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0));
 }
 template void coarse_assemble<double>(cudaStream_t, const Grid&, const Mat&, int, const double*,
                                       double*, double*);
@@ -681,7 +681,7 @@ __global__ void k_coarse_factor(int n, T* A, const T* diag0) {
 }
 template <class T>
 void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0) {
-  k_coarse_factor<<<1, 1024, 0, s>>>(n, A, diag0);
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_factor<<<1, 1024, 0, s>>>(n, A, diag0));
 }
 template void coarse_factor<double>(cudaStream_t, int, double*, const double*);
 template void coarse_factor<float>(cudaStream_t, int, float*, const float*);
@@ -710,7 +710,7 @@ __global__ void k_coarse_solve(int n, const T* L, const T* b, T* x) {
 }
 template <class T>
 void coarse_solve(cudaStream_t s, int n, const T* L, const T* b, T* x) {
-  k_coarse_solve<<<1, 256, n * sizeof(T), s>>>(n, L, b, x);
+  PF_LAUNCH(kclass(KC_COARSE, false, false), 0.0, s, k_coarse_solve<<<1, 256, n * sizeof(T), s>>>(n, L, b, x));
 }
 template void coarse_solve<double>(cudaStream_t, int, const double*, const double*, double*);
 template void coarse_solve<float>(cudaStream_t, int, const float*, const float*, float*);
@@ -745,14 +745,14 @@ __global__ void k_merit_parts(Grid g, const double* x, const double* F, const do
 }
 void merit_parts(cudaStream_t s, const Grid& g, const double* x, const double* F,
                  const double* lo, double* v, double* dg) {
-  k_merit_parts<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, x, F, lo, v, dg);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_merit_parts<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, x, F, lo, v, dg));
 }
 __global__ void k_merit_dir(size_t n, const double* dg, const double* Hv, double* d) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) d[i] = -(dg[i] + Hv[i]);
 }
 void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d) {
-  k_merit_dir<<<nblocks(n), RED_THREADS, 0, s>>>(n, dg, Hv, d);
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_merit_dir<<<nblocks(n), RED_THREADS, 0, s>>>(n, dg, Hv, d));
 }
 
 }  // namespace pf

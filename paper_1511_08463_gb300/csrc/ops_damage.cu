@@ -4,11 +4,27 @@
 
 namespace pf {
 
+template <class T>
+static double damage_bytes(const Grid& g, int mode, const DamageArgs<T>& a) {
+  const double t = sizeof(T);
+  double node = 0.0;
+  switch (mode) {
+    case M_APPLY: node = 2 * t; break;
+    case M_MASKED: node = 2 * t; break;
+    case M_RESB: node = 3 * t; break;
+    case M_CHEB: node = (a.d ? 6 : 5) * t; break;
+    case M_GRAD: node = 5 * t + 1; break;
+    case M_TRIAL: node = 7 * t + 1; break;
+  }
+  if (a.excl) node += 1;
+  return double(g.n) * node + double(g.nelem) * t;
+}
+
 template <class Op>
-static void launch_op(cudaStream_t s, const Op& op) {
+static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
   dim3 block(TX, TY);
   dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
-  stencil_kernel<Op><<<grid, block, 0, s>>>(op);
+  PF_LAUNCH(id, bytes, s, stencil_kernel<Op><<<grid, block, 0, s>>>(op));
 }
 
 template <class T, int K, int M, bool D>
@@ -17,7 +33,9 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>&
   op.g = g;
   op.m = m;
   op.args = a;
-  launch_op(s, op);
+  const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED : M == M_RESB ? KC_DM_RESB
+                 : M == M_CHEB ? KC_DM_CHEB : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;
+  launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse != 0), damage_bytes<T>(g, M, a));
 }
 
 template <class T, int K>

@@ -3,11 +3,27 @@
 
 namespace pf {
 
+// algorithmic bytes of one launch: compulsory reads and writes of the operator on its grid
+template <class T>
+static double elastic_bytes(const Grid& g, int coef, int mode, const ElasticArgs<T>& a) {
+  const double t = sizeof(T);
+  double node = 0.0;
+  switch (mode) {
+    case M_APPLY:
+    case M_MASKED: node = 4 * t; break;
+    case M_RESB: node = 6 * t; break;
+    case M_RESID: node = 4 * t; break;
+    case M_CHEB: node = (a.d ? 12 : 10) * t; break;
+  }
+  double coefb = coef == COEF_ALPHA ? double(g.n) * t : double(g.nelem) * t;
+  return double(g.n) * node + coefb;
+}
+
 template <class Op>
-static void launch_op(cudaStream_t s, const Op& op) {
+static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
   dim3 block(TX, TY);
   dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
-  stencil_kernel<Op><<<grid, block, 0, s>>>(op);
+  PF_LAUNCH(id, bytes, s, stencil_kernel<Op><<<grid, block, 0, s>>>(op));
 }
 
 template <class T, int K, int C, int M, bool E, bool D>
@@ -16,7 +32,9 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>
   op.g = g;
   op.m = m;
   op.args = a;
-  launch_op(s, op);
+  const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
+                 : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;
+  launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse != 0), elastic_bytes<T>(g, C, M, a));
 }
 
 template <class T, int K>

@@ -1,0 +1,37 @@
+// Launch accounting and optional CUDA-event timing of kernel classes.
+//
+// Every kernel launch of the library goes through PF_LAUNCH, which counts it and, when timing
+// is enabled for its class, brackets it with two events recorded on the launching stream.  The
+// algorithmic bytes of each launch (compulsory reads and writes of the operator on its grid) are
+// accumulated beside the measured time so achieved bandwidth can be computed per class.
+// Process-wide state; not thread-safe (timing is meant for single-threaded measurement runs).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pf {
+
+enum KernelClass : int {
+  KC_EL_APPLY = 0, KC_EL_MASKED, KC_EL_RESB, KC_EL_RESID, KC_EL_CHEB,
+  KC_DM_APPLY, KC_DM_MASKED, KC_DM_RESB, KC_DM_CHEB, KC_DM_GRAD, KC_DM_TRIAL,
+  KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_BASE_COUNT
+};
+// class id = base + KC_BASE_COUNT * variant, variant = (fp64 ? 2 : 0) + (coarse level ? 1 : 0)
+constexpr int KC_COUNT = KC_BASE_COUNT * 4;
+
+inline int kclass(int base, bool fp64, bool coarse) {
+  return base + KC_BASE_COUNT * ((fp64 ? 2 : 0) + (coarse ? 1 : 0));
+}
+
+void prof_pre(int id, cudaStream_t s);
+void prof_post(int id, double bytes, cudaStream_t s);
+const char* kclass_name(int id);
+
+}  // namespace pf
+
+#define PF_LAUNCH(ID, BYTES, STREAM, ...)      \
+  do {                                         \
+    ::pf::prof_pre((ID), (STREAM));            \
+    __VA_ARGS__;                               \
+    ::pf::prof_post((ID), (BYTES), (STREAM));  \
+  } while (0)

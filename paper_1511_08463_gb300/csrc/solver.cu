@@ -258,6 +258,7 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
     a.coef = L.buf<T>().coefE;
     a.y = y;
     a.slot = slot(s, sl);
+    a.coarse = l > 0;
     launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_MASKED, false, dot, a);
   } else {
     DamageArgs<T> a{};
@@ -266,6 +267,7 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
     a.excl = l == 0 ? s.act : nullptr;
     a.y = y;
     a.slot = slot(s, sl);
+    a.coarse = l > 0;
     launch_damage<T>(st, L.g, s.m, M_MASKED, dot, a);
   }
 }
@@ -280,6 +282,7 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     a.coef = L.buf<T>().coefE;
     a.b = b;
     a.y = r;
+    a.coarse = l > 0;
     launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_RESB, false, false, a);
   } else {
     DamageArgs<T> a{};
@@ -288,6 +291,7 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     a.excl = l == 0 ? s.act : nullptr;
     a.b = b;
     a.y = r;
+    a.coarse = l > 0;
     launch_damage<T>(st, L.g, s.m, M_RESB, false, a);
   }
 }
@@ -308,6 +312,7 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.cr = T(cr);
     a.y = xo;
     a.dout = dout;
+    a.coarse = l > 0;
     launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_CHEB, false, false, a);
   } else {
     DamageArgs<T> a{};
@@ -321,6 +326,7 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.cr = T(cr);
     a.y = xo;
     a.dout = dout;
+    a.coarse = l > 0;
     launch_damage<T>(st, L.g, s.m, M_CHEB, false, a);
   }
 }

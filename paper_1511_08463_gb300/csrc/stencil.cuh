@@ -144,6 +144,7 @@ struct ElasticArgs {
   T* y;               // output (2n); M_CHEB: new x
   T* dout;            // M_CHEB: new d
   RedSlot slot;
+  int coarse;         // launch accounting: 1 on coarse multigrid levels
 };
 
 template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT>
@@ -273,6 +274,7 @@ struct DamageArgs {
   T* xt;                // M_TRIAL: trial point
   uint8_t* act;         // M_GRAD/M_TRIAL: active flags written
   RedSlot slot;
+  int coarse;           // launch accounting: 1 on coarse multigrid levels
 };
 
 template <class T, int KIND_, int MODE, bool DOT>
@@ -308,7 +310,7 @@ struct DamageOp {
       v.p = T(fmin(fmax(z, l), h));
     } else {
       v.p = args.x[node];
-      if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl[node]) v.p = T(0);
+      if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = T(0);
     }
     return v;
   }
@@ -347,16 +349,16 @@ struct DamageOp {
       args.y[node] = f;
       if (DOT) red[0] += double(own.p) * double(f);
     } else if (MODE == M_MASKED) {
-      T v = args.excl[node] ? T(0) : f;
+      T v = (args.excl && args.excl[node]) ? T(0) : f;
       args.y[node] = v;
       if (DOT) red[0] += double(own.p) * double(v);
     } else if (MODE == M_RESB) {
-      T r = args.excl[node] ? T(0) : args.b[node] - f;
+      T r = (args.excl && args.excl[node]) ? T(0) : args.b[node] - f;
       args.y[node] = r;
       if (DOT) red[0] += double(r) * double(r);
     } else if (MODE == M_CHEB) {
       T dp = args.d ? args.d[node] : T(0);
-      T dn = args.excl[node] ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
+      T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
       args.dout[node] = dn;
       args.y[node] = own.p + dn;
     } else {  // M_GRAD / M_TRIAL (T = double)

@@ -59,8 +59,9 @@ def test_alpha_solve(model, precision):
     g.set_fields(u=u, alpha=ap, alpha_prev=ap)
     g.set_load(0.0, 0.0)
     rep = g.alpha_solve(tight_opts(S, precision=precision))
-    p.u, p.alpha, p.alpha_prev = u, ap.copy(), ap.copy()
-    aref, info = am.solve_alpha(p, u, ap.copy(), 0.0)
+    p.u, p.alpha, p.alpha_prev = u.copy(), ap.copy(), ap.copy()
+    p.lift(0.0)  # the same Dirichlet lift the GPU applied in set_load
+    aref, info = am.solve_alpha(p, p.u, ap.copy(), 0.0)
     _, a, _ = g.get_fields()
     assert np.abs(a - aref).max() <= 1e-8
     assert 0 < np.sum((aref > ap + 1e-12)) < aref.size  # a genuine box-constrained solve

@@ -112,10 +112,11 @@ def bar(nx: int = 128, ny: int = 16, n_steps: int = 20, ell: float = 0.05, model
     tc = bar_critical_displacement(lx, 1.0, nu, 1.0, ell)
     loads = [(load_factor * tc * k / n_steps, 0.0) for k in range(1, n_steps + 1)]
     boxes = []
-    if seed_column:  # symmetry-breaking seed at x = L/2 (vertex column)
+    if seed_column:  # symmetry-breaking seed on the vertex column one cell right of x = L/2
+        # (x = L/2 itself is the centre of the mesh's 180-degree rotation symmetry)
         if nx % 2:
             raise ValueError("nx must be even for the seed column")
-        boxes.append((nx, nx, 0, 2 * ny, 1e-3))
+        boxes.append((nx + 2, nx + 2, 0, 2 * ny, 1e-3))
     return Workload(
         name=f"bar_{nx}x{ny}", kind="right", nx=nx, ny=ny, x0=0.0, y0=0.0, lx=lx, ly=ly,
         nu=nu, ell=ell, model=model, k_ell=k_ell,
