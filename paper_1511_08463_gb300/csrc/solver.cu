@@ -103,6 +103,8 @@ pf_status validate(const pf_mesh_desc* d) {
   if (d->nx < 1 || d->ny < 1 || d->nx > 65536 || d->ny > 65536)
     return fail(PF_EINVAL, "mesh size %d x %d out of range", d->nx, d->ny);
   if (!(d->lx > 0) || !(d->ly > 0)) return fail(PF_EINVAL, "domain size must be positive");
+  if (2.0 * (double(d->nx) + 1.0) * (double(d->ny) + 1.0) > 2147483647.0)
+    return fail(PF_EINVAL, "mesh %d x %d has too many nodes", d->nx, d->ny);
   if (d->n_pins < 0 || d->n_pins > PF_MAX_PINS) return fail(PF_EINVAL, "bad pin count");
   if (d->n_boxes < 0 || d->n_boxes > PF_MAX_BOXES) return fail(PF_EINVAL, "bad box count");
   for (int k = 0; k < d->n_pins; ++k) {
