@@ -241,6 +241,22 @@ pf_status pf_op_alpha_solve(pf_sim* sim, const pf_solver_opts* o, void* stream,
  * E_alpha) at the resident state and current load.  Synchronous. */
 pf_status pf_op_full_residual(pf_sim* sim, double* phi_norm, void* stream);
 
+/* Energies (elastic, surface, total) of caller-given fields, like pf_energy, but without any
+ * device memory allocation and without a sim.  No counterpart in the paper: it exists for callers
+ * that cannot let a library call cudaMalloc/cudaFree -- for example an application whose memory
+ * pool already owns all free device memory, or code that must not trigger the implicit device
+ * synchronization those calls may perform.
+ * d, m, L: host descriptors as for pf_create_mesh / pf_set_material / pf_load_step (the thermal
+ * eigenstrain uses L->dT). u (2*n_nodes doubles, interleaved) and alpha (n_nodes doubles):
+ * device pointers owned by the caller, node order as above.  out: host, 3 doubles.
+ * Scratch: a fixed 328 KB array compiled into the library, held on every device that loads it
+ * until the process exits.  Limit: at most 8192 cell rows (ny); larger meshes return PF_EINVAL
+ * with a message.  The first call on a device looks up the array's device address (do this
+ * first call before any stream capture).  All calls on a device share the array and reuse its
+ * previous contents, so calls that overlap on the GPU race; serialize them.  Synchronous. */
+pf_status pf_energy_noalloc(const pf_mesh_desc* d, const pf_material* m, const pf_load* L,
+                            const double* u, const double* alpha, double out[3], void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Launch accounting and kernel timing (tracing support; process-wide, not thread-safe).
  * Every kernel the library launches is counted.  With timing enabled, each launch of the

@@ -95,6 +95,8 @@ _SIGS = {
     "pf_op_alpha_solve": (C.c_int, [_VP, C.POINTER(pf_solver_opts), _VP,
                                     C.POINTER(pf_step_report)]),
     "pf_op_full_residual": (C.c_int, [_VP, C.POINTER(C.c_double), _VP]),
+    "pf_energy_noalloc": (C.c_int, [C.POINTER(pf_mesh_desc), C.POINTER(pf_material),
+                                    C.POINTER(pf_load), _VP, _VP, C.POINTER(C.c_double), _VP]),
     "pf_prof_enable": (C.c_int, [C.c_int, C.c_int]),
     "pf_prof_reset": (C.c_int, []),
     "pf_launch_count": (C.c_int64, []),

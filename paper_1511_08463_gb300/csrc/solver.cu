@@ -27,6 +27,9 @@ static pf_status fail(pf_status st, const char* fmt, ...) {
   g_err = buf;
   return st;
 }
+namespace pf {
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace pf
 #define CU(call)                                                                       \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
@@ -750,6 +753,43 @@ pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step
 
 }  // namespace
 
+namespace pf {
+pf_status describe_mesh(const pf_mesh_desc* d, Grid* g) {
+  pf_status st = validate(d);
+  if (st != PF_OK) return st;
+  *g = make_grid(*d, 0);
+  return PF_OK;
+}
+
+// kernel constants of a material for callers without a sim (the same constants pf_set_material
+// stores in a sim)
+pf_status describe_material(const pf_material* mi, Mat* out) {
+  if (!mi || !out) return fail(PF_EINVAL, "null argument");
+  if (!(mi->E > 0) || !(mi->Gc > 0) || !(mi->ell > 0) || !(mi->k_ell >= 0) || !(mi->nu > -1.0) ||
+      !(mi->nu < 0.5))
+    return fail(PF_EINVAL, "invalid material constants");
+  if (mi->model != PF_AT1 && mi->model != PF_AT2) return fail(PF_EINVAL, "unknown damage model");
+  if (mi->plane != PF_PLANE_STRAIN && mi->plane != PF_PLANE_STRESS)
+    return fail(PF_EINVAL, "unknown plane assumption");
+  if (mi->beta != 0.0 && !(mi->pen > 0)) return fail(PF_EINVAL, "penetration length must be positive");
+  Mat m{};
+  double E = mi->E, nu = mi->nu;
+  m.mu = E / (2.0 * (1.0 + nu));
+  m.lam = mi->plane == PF_PLANE_STRAIN ? E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) : E * nu / (1.0 - nu * nu);
+  m.lam2mu = m.lam + 2.0 * m.mu;
+  m.k_ell = mi->k_ell;
+  double cw = mi->model == PF_AT1 ? 8.0 / 3.0 : 2.0;  // c_w = 4 int_0^1 sqrt(w)
+  m.c1 = 2.0 * mi->Gc * mi->ell / cw;
+  m.c2 = mi->model == PF_AT2 ? 2.0 * mi->Gc / (cw * mi->ell) : 0.0;
+  m.c3 = mi->model == PF_AT1 ? mi->Gc / (cw * mi->ell) : 0.0;
+  m.gc_cw = mi->Gc / cw;
+  m.ell = mi->ell;
+  m.model = mi->model;
+  *out = m;
+  return PF_OK;
+}
+}  // namespace pf
+
 // =============================================================================================
 // C ABI
 // =============================================================================================
@@ -903,6 +943,8 @@ pf_status pf_set_material(pf_sim* s, const pf_material* mi) {
   s->elastic_ready64 = s->elastic_ready32 = false;
   return PF_OK;
 }
+
+
 
 static pf_status check_opts(const pf_solver_opts* o) {
   if (!o) return fail(PF_EINVAL, "null options");

@@ -50,6 +50,11 @@ enum Slot {
   S_TMP = 16, S_COUNT = 32
 };
 
+// shared with other translation units of the library
+void set_error_message(const char* msg);
+pf_status describe_mesh(const pf_mesh_desc* d, Grid* g);      // validate + level-0 grid
+pf_status describe_material(const pf_material* m, Mat* out);  // validate + kernel constants
+
 }  // namespace pf
 
 struct pf_sim {
