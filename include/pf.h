@@ -122,7 +122,8 @@ typedef struct pf_solver_opts {
   double switch_tol, newton_rtol;
   int32_t newton_maxit, minres_maxit;
   double minres_rtol;
-  int32_t use_graphs;      /* reserved: 0 */
+  int32_t use_graphs;      /* 1 (default): each PCG solve runs as one CUDA graph with a device-side
+                            * loop; 0: host-driven iterations */
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step). */

@@ -34,6 +34,10 @@ template <class T>
 void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
                  const double* rz_old);
 
+// end of a graph-resident CG iteration: rz_old <- rz_new, it += 1, keep looping while
+// rr > tol2 and it < maxit (sets the while-condition of the graph)
+void cg_control(cudaStream_t s, cudaGraphConditionalHandle h, double* rz_new, double* rz_old,
+                const double* rr, const double* tol2, double* it, const double* maxit);
 // u <- u + omega (xt - u); reductions: max |du|, max |u_new|
 void relax_u(cudaStream_t s, double* u, const double* xt, double omega, size_t n2, RedSlot slot);
 // max feasible step along alpha + w (at - alpha) in [lo, hi]: out = -min ratio (MAX reduction)
@@ -75,7 +79,7 @@ void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* 
 // prescribed components set to 0.
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                  const T* rf, T* bc);
+                  const T* rf, T* bc, const uint8_t* excl_c);  // excl_c (may be null): zeroed
 // xf += P xc on free components; excl (fine, may be null) zeroes excluded nodes
 template <class T>
 void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
@@ -84,11 +88,15 @@ void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int 
 // ---- coarsest level dense solve -----------------------------------------------------------------
 template <class T>
 void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef,
-                     T* A, T* diag0);
+                     T* A, T* diag0, const uint8_t* excl);  // excl (may be null): identity rows
+// coarse active-set mask from the fine one (coincident nodes)
+void mask_restrict(cudaStream_t s, const Grid& gf, const Grid& gc, const uint8_t* ef, uint8_t* ec);
 template <class T>
 void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0);
 template <class T>
-void coarse_solve(cudaStream_t s, int n, const T* L, const T* b, T* x);
+void coarse_invert(cudaStream_t s, int n, const T* L, T* Ainv);  // explicit inverse from L
+template <class T>
+void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x);  // x = Ainv b
 
 // ---- misc for the damage solve ------------------------------------------------------------------
 // steepest-descent fallback of Algorithm 4: v = -pb qb Phi, dg = (pa - pb qa) Phi

@@ -78,11 +78,11 @@ template void vec_mul<float>(cudaStream_t, float*, const float*, const float*, s
 
 template <class T>
 __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
-  double v[1] = {0.0};
+  T v[1] = {T(0)};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    v[0] += double(x[i]) * double(y[i]);
-  block_reduce_finalize<1, false>(v, slot);
+    v[0] += x[i] * y[i];
+  block_reduce_finalize<1, false, T>(v, slot);
 }
 template <class T>
 void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot) {
@@ -94,17 +94,19 @@ template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, R
 template <class T>
 __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
                         const double* pAp, RedSlot slot) {
-  const double a = *rz / *pAp;
-  const T at = T(a);
-  double v[1] = {0.0};
+  __shared__ T sa;  // step length computed once per block
+  if (threadIdx.x == 0) sa = T(*rz / *pAp);
+  __syncthreads();
+  const T at = sa;
+  T v[1] = {T(0)};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     x[i] += at * p[i];
     T ri = r[i] - at * Ap[i];
     r[i] = ri;
-    v[0] += double(ri) * double(ri);
+    v[0] += ri * ri;
   }
-  block_reduce_finalize<1, false>(v, slot);
+  block_reduce_finalize<1, false, T>(v, slot);
 }
 template <class T>
 void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
@@ -118,14 +120,14 @@ template void cg_update_xr<float>(cudaStream_t, float*, float*, const float*, co
 
 template <class T>
 __global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const double* rz_old) {
+  __shared__ T sb;  // conjugation coefficient computed once per block
+  // beta = 0 (first iteration: *rz_old == 0, or no old value given) means p = z, and p is not
+  // read (it may hold stale values)
+  if (threadIdx.x == 0) sb = (rz_old && *rz_old != 0.0) ? T(*rz_new / *rz_old) : T(0);
+  __syncthreads();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (rz_old == nullptr) {
-    p[i] = z[i];
-  } else {
-    const T b = T(*rz_new / *rz_old);
-    p[i] = z[i] + b * p[i];
-  }
+  p[i] = sb != T(0) ? z[i] + sb * p[i] : z[i];
 }
 template <class T>
 void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
@@ -136,6 +138,23 @@ template void cg_update_p<double>(cudaStream_t, double*, const double*, size_t, 
                                   const double*);
 template void cg_update_p<float>(cudaStream_t, float*, const float*, size_t, const double*,
                                  const double*);
+
+// End of one graph-resident CG iteration: rz_old <- rz_new, count the iteration and decide on
+// the device whether the while-loop of the graph runs again.
+__global__ void k_cg_control(cudaGraphConditionalHandle h, double* rz_new, double* rz_old,
+                             const double* rr, const double* tol2, double* it, const double* maxit) {
+  *rz_old = *rz_new;
+  double k = *it + 1.0;
+  *it = k;
+  double r = *rr;
+  bool go = (r > *tol2) && (k < *maxit) && (r == r);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+void cg_control(cudaStream_t s, cudaGraphConditionalHandle h, double* rz_new, double* rz_old,
+                const double* rr, const double* tol2, double* it, const double* maxit) {
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s,
+            k_cg_control<<<1, 1, 0, s>>>(h, rz_new, rz_old, rr, tol2, it, maxit));
+}
 
 // over-relaxation of u (Algorithm 2): prescribed dofs have xt == u, so they do not move
 __global__ void k_relax_u(double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
@@ -429,62 +448,62 @@ __device__ __forceinline__ int node_elements(const Grid& g, int node, int* cells
 // l1 row sums of the assembled element matrices: D_ii = sum_T sum_j |K_T(i, j)|, so that the
 // spectrum of D^{-1} K lies in (0, 1].
 template <class T>
-__global__ void k_l1_elastic(Grid g, Mat m, const T* coef, T* dinv) {
+__global__ void k_l1_elastic(Grid g, Consts<T> cs, const T* coef, T* dinv) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int cells[8], ts[8], ks[8];
   int cnt = node_elements(g, node, cells, ts, ks);
   int NE = elems_per_cell(g.kind);
-  double dx = 0.0, dy = 0.0;
+  T dx = T(0), dy = T(0);
   for (int e = 0; e < cnt; ++e) {
     int t = ts[e], k = ks[e];
-    double w = double(coef[cells[e] * NE + t]) * g.area;
-    double gkx = gxr(g.kind, t, k) * g.ihx, gky = gyr(g.kind, t, k) * g.ihy;
-    double sx = 0.0, sy = 0.0;
+    T w = coef[cells[e] * NE + t] * cs.area;
+    T gkx = T(gxr(g.kind, t, k)) * cs.ihx, gky = T(gyr(g.kind, t, k)) * cs.ihy;
+    T sx = T(0), sy = T(0);
     for (int l = 0; l < 3; ++l) {
-      double glx = gxr(g.kind, t, l) * g.ihx, gly = gyr(g.kind, t, l) * g.ihy;
-      sx += fabs(gkx * glx * m.lam2mu + gky * gly * m.mu) + fabs(gkx * gly * m.lam + gky * glx * m.mu);
-      sy += fabs(gky * glx * m.lam + gkx * gly * m.mu) + fabs(gky * gly * m.lam2mu + gkx * glx * m.mu);
+      T glx = T(gxr(g.kind, t, l)) * cs.ihx, gly = T(gyr(g.kind, t, l)) * cs.ihy;
+      sx += fabs(gkx * glx * cs.lam2mu + gky * gly * cs.mu) + fabs(gkx * gly * cs.lam + gky * glx * cs.mu);
+      sy += fabs(gky * glx * cs.lam + gkx * gly * cs.mu) + fabs(gky * gly * cs.lam2mu + gkx * glx * cs.mu);
     }
     dx += w * sx;
     dy += w * sy;
   }
   int X2, Y2;
   node_coords(g, node, X2, Y2);
-  dinv[2 * node] = (is_fixed(g, X2, Y2, 0) || dx <= 0.0) ? T(0) : T(1.0 / dx);
-  dinv[2 * node + 1] = (is_fixed(g, X2, Y2, 1) || dy <= 0.0) ? T(0) : T(1.0 / dy);
+  dinv[2 * node] = (is_fixed(g, X2, Y2, 0) || dx <= T(0)) ? T(0) : T(1) / dx;
+  dinv[2 * node + 1] = (is_fixed(g, X2, Y2, 1) || dy <= T(0)) ? T(0) : T(1) / dy;
 }
 template <class T>
 void l1_dinv_elastic(cudaStream_t s, const Grid& g, const Mat& m, const T* coef, T* dinv) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, coef, dinv));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, make_consts<T>(g, m), coef, dinv));
 }
 template void l1_dinv_elastic<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_elastic<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
 
 template <class T>
-__global__ void k_l1_damage(Grid g, Mat m, const T* w, T* dinv) {
+__global__ void k_l1_damage(Grid g, Consts<T> cs, const T* w, T* dinv) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int cells[8], ts[8], ks[8];
   int cnt = node_elements(g, node, cells, ts, ks);
   int NE = elems_per_cell(g.kind);
-  double dd = 0.0;
+  T dd = T(0);
   for (int e = 0; e < cnt; ++e) {
     int t = ts[e], k = ks[e];
-    double me = double(w[cells[e] * NE + t]) * g.area / 12.0;
-    double gkx = gxr(g.kind, t, k) * g.ihx, gky = gyr(g.kind, t, k) * g.ihy;
+    T me = w[cells[e] * NE + t] * cs.area * T(1.0 / 12.0);
+    T gkx = T(gxr(g.kind, t, k)) * cs.ihx, gky = T(gyr(g.kind, t, k)) * cs.ihy;
     for (int l = 0; l < 3; ++l) {
-      double glx = gxr(g.kind, t, l) * g.ihx, gly = gyr(g.kind, t, l) * g.ihy;
-      dd += fabs(me * (l == k ? 2.0 : 1.0) + m.c1 * g.area * (gkx * glx + gky * gly));
+      T glx = T(gxr(g.kind, t, l)) * cs.ihx, gly = T(gyr(g.kind, t, l)) * cs.ihy;
+      dd += fabs(me * (l == k ? T(2) : T(1)) + cs.c1 * cs.area * (gkx * glx + gky * gly));
     }
   }
   int X2, Y2;
   node_coords(g, node, X2, Y2);
-  dinv[node] = (is_fixed(g, X2, Y2, 2) || dd <= 0.0) ? T(0) : T(1.0 / dd);
+  dinv[node] = (is_fixed(g, X2, Y2, 2) || dd <= T(0)) ? T(0) : T(1) / dd;
 }
 template <class T>
 void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* dinv) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, m, w, dinv));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, make_consts<T>(g, m), w, dinv));
 }
 template void l1_dinv_damage<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_damage<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -504,7 +523,8 @@ __device__ __forceinline__ T fget(const Grid& gf, const T* v, bool centre, int i
 }
 
 template <class T>
-__global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* rf, T* bc) {
+__global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* rf, T* bc,
+                           const uint8_t* excl_c) {
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= gc.n) return;
   int X2, Y2;
@@ -531,19 +551,19 @@ __global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* 
             fget(gf, rf, true, 2 * I + 1, 2 * J + 1, c, ncomp);
       acc += T(0.5) * h;
     }
-    if (is_fixed(gc, X2, Y2, comp_base + c)) acc = T(0);
+    if (is_fixed(gc, X2, Y2, comp_base + c) || (excl_c && excl_c[node])) acc = T(0);
     bc[node * ncomp + c] = acc;
   }
 }
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                  const T* rf, T* bc) {
-  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc));
+                  const T* rf, T* bc, const uint8_t* excl_c) {
+  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc, excl_c));
 }
 template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
-                                   double*);
+                                   double*, const uint8_t*);
 template void restrict_res<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
-                                  float*);
+                                  float*, const uint8_t*);
 
 template <class T>
 __device__ __forceinline__ T cget(const Grid& gc, const T* v, bool centre, int I, int J, int c,
@@ -593,7 +613,8 @@ template void prolong_add<float>(cudaStream_t, const Grid&, const Grid&, int, in
 // coarsest level: dense assembly, Cholesky and triangular solves in one thread block
 // ---------------------------------------------------------------------------------------------
 template <class T>
-__global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* A, T* diag0) {
+__global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* A, T* diag0,
+                                  const uint8_t* excl) {
   // block = column j, threads = rows i
   const int ncomp = physics == 0 ? 2 : 1;
   const int nd = g.n * ncomp;
@@ -601,13 +622,13 @@ __global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* 
   int nj = col / ncomp, cjc = col % ncomp;
   int X2j, Y2j;
   node_coords(g, nj, X2j, Y2j);
-  bool fj = is_fixed(g, X2j, Y2j, physics == 0 ? cjc : 2);
+  bool fj = is_fixed(g, X2j, Y2j, physics == 0 ? cjc : 2) || (excl && excl[nj]);
   int NE = elems_per_cell(g.kind);
   for (int row = threadIdx.x; row < nd; row += blockDim.x) {
     int ni = row / ncomp, cic = row % ncomp;
     int X2i, Y2i;
     node_coords(g, ni, X2i, Y2i);
-    bool fi = is_fixed(g, X2i, Y2i, physics == 0 ? cic : 2);
+    bool fi = is_fixed(g, X2i, Y2i, physics == 0 ? cic : 2) || (excl && excl[ni]);
     double acc = 0.0;
     if (fi || fj) {
       acc = (row == col) ? 1.0 : 0.0;
@@ -645,14 +666,29 @@ __global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* 
 }
 template <class T>
 void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef, T* A,
-                     T* diag0) {
+                     T* diag0, const uint8_t* excl) {
   int nd = g.n * (physics == 0 ? 2 : 1);
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0, excl));
 }
 template void coarse_assemble<double>(cudaStream_t, const Grid&, const Mat&, int, const double*,
-                                      double*, double*);
+                                      double*, double*, const uint8_t*);
 template void coarse_assemble<float>(cudaStream_t, const Grid&, const Mat&, int, const float*,
-                                     float*, float*);
+                                     float*, float*, const uint8_t*);
+
+// Active-set mask of a coarse level: a coarse node is excluded iff the fine node at the same
+// position is excluded (coarse vertex (I,J) = fine vertex (2I,2J); coarse centre (I,J) = fine
+// vertex (2I+1, 2J+1)).
+__global__ void k_mask_restrict(Grid gf, Grid gc, const uint8_t* ef, uint8_t* ec) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= gc.n) return;
+  int X2, Y2;
+  node_coords(gc, node, X2, Y2);
+  ec[node] = ef[Y2 * (gf.nx + 1) + X2];  // the fine vertex (X2, Y2) coincides with this node
+}
+void mask_restrict(cudaStream_t s, const Grid& gf, const Grid& gc, const uint8_t* ef, uint8_t* ec) {
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s,
+            k_mask_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ef, ec));
+}
 
 // In-place Cholesky A = L L^T (lower triangle); a pivot that is not positive relative to the
 // original diagonal is replaced by that diagonal (a regularized factorization, acceptable for a
@@ -686,13 +722,15 @@ void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0) {
 template void coarse_factor<double>(cudaStream_t, int, double*, const double*);
 template void coarse_factor<float>(cudaStream_t, int, float*, const float*);
 
+// Column j of A^{-1} from the Cholesky factor (one block per column; set-up time only).
 template <class T>
-__global__ void k_coarse_solve(int n, const T* L, const T* b, T* x) {
+__global__ void k_coarse_invert(int n, const T* L, T* Ainv) {
   extern __shared__ unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = b[i];
+  const int j = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == j) ? T(1) : T(0);
   __syncthreads();
-  for (int k = 0; k < n; ++k) {  // forward: L y = b
+  for (int k = 0; k < n; ++k) {  // forward: L y = e_j
     if (threadIdx.x == 0) y[k] /= L[(size_t)k * n + k];
     __syncthreads();
     T yk = y[k];
@@ -706,11 +744,32 @@ __global__ void k_coarse_solve(int n, const T* L, const T* b, T* x) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] -= L[(size_t)k * n + i] * yk;
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Ainv[(size_t)j * n + i] = y[i];
 }
 template <class T>
-void coarse_solve(cudaStream_t s, int n, const T* L, const T* b, T* x) {
-  PF_LAUNCH(kclass(KC_COARSE, false, false), 0.0, s, k_coarse_solve<<<1, 256, n * sizeof(T), s>>>(n, L, b, x));
+void coarse_invert(cudaStream_t s, int n, const T* L, T* Ainv) {
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_invert<<<n, 128, n * sizeof(T), s>>>(n, L, Ainv));
+}
+template void coarse_invert<double>(cudaStream_t, int, const double*, double*);
+template void coarse_invert<float>(cudaStream_t, int, const float*, float*);
+
+// x = A^{-1} b with the stored symmetric inverse: thread i reads column i (coalesced).
+template <class T>
+__global__ void k_coarse_solve(int n, const T* Ainv, const T* b, T* x) {
+  extern __shared__ unsigned char smem_raw[];
+  T* bs = reinterpret_cast<T*>(smem_raw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = b[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T acc = T(0);
+    for (int j = 0; j < n; ++j) acc += Ainv[(size_t)j * n + i] * bs[j];
+    x[i] = acc;
+  }
+}
+template <class T>
+void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x) {
+  int threads = n < 1024 ? ((n + 31) / 32) * 32 : 1024;
+  PF_LAUNCH(kclass(KC_COARSE, false, false), 0.0, s, k_coarse_solve<<<1, threads, n * sizeof(T), s>>>(n, Ainv, b, x));
 }
 template void coarse_solve<double>(cudaStream_t, int, const double*, const double*, double*);
 template void coarse_solve<float>(cudaStream_t, int, const float*, const float*, float*);

@@ -32,6 +32,7 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>&
   DamageOp<T, K, M, D> op;
   op.g = g;
   op.m = m;
+  op.cs = make_consts<T>(g, m);
   op.args = a;
   const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED : M == M_RESB ? KC_DM_RESB
                  : M == M_CHEB ? KC_DM_CHEB : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;

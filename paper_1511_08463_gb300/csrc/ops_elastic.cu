@@ -31,6 +31,7 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>
   ElasticOp<T, K, C, M, E, D> op;
   op.g = g;
   op.m = m;
+  op.cs = make_consts<T>(g, m);
   op.args = a;
   const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
                  : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;

@@ -58,6 +58,7 @@ struct Grid {
   uint8_t fixed[4][3];             // [edge][comp] (edges: left, right, bottom, top)
   int npins;
   int pin_x2[PF_MAX_PINS], pin_y2[PF_MAX_PINS], pin_comp[PF_MAX_PINS];
+  int interior_pins;  // 1 if some pin lies strictly inside the rectangle
 };
 
 // Material constants in the form the kernels use.
@@ -72,6 +73,8 @@ struct Mat {
 };
 
 __device__ __forceinline__ bool is_fixed(const Grid& g, int X2, int Y2, int comp) {
+  // interior nodes are free unless a pin sits off the boundary (rare): skip the pin loop
+  if (!g.interior_pins && X2 > 0 && X2 < 2 * g.nx && Y2 > 0 && Y2 < 2 * g.ny) return false;
   bool f = (X2 == 0 && g.fixed[0][comp]) || (X2 == 2 * g.nx && g.fixed[1][comp]) ||
            (Y2 == 0 && g.fixed[2][comp]) || (Y2 == 2 * g.ny && g.fixed[3][comp]);
   for (int k = 0; k < g.npins; ++k)
@@ -116,8 +119,8 @@ struct RedSlot {
   double* out;       // NV doubles
 };
 
-template <int NV, bool MAX>
-__device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], RedSlot slot) {
+template <int NV, bool MAX, class VT = double>
+__device__ __forceinline__ void block_reduce_finalize(VT (&v)[NV], RedSlot slot) {
   __shared__ double red[NV][32];
   __shared__ bool last;
   int lane = threadIdx.x & 31, warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
@@ -127,12 +130,12 @@ __device__ __forceinline__ void block_reduce_finalize(double (&v)[NV], RedSlot s
   warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    double x = v[q];
+    VT x = v[q];  // warp stage in the partials' own precision, then FP64 across warps
     for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_down_sync(0xffffffffu, x, o);
-      x = MAX ? fmax(x, y) : x + y;
+      VT y = __shfl_down_sync(0xffffffffu, x, o);
+      x = MAX ? (x > y ? x : y) : x + y;
     }
-    if (lane == 0) red[q][warp] = x;
+    if (lane == 0) red[q][warp] = double(x);
   }
   __syncthreads();
   int nwarps = (nthreads + 31) >> 5;

@@ -24,6 +24,7 @@ struct State {
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
   cudaEvent_t open_a = nullptr;
+  bool capturing = false;
   int open_id = -1;
   int64_t timed_launches[KC_COUNT] = {};
   double ms[KC_COUNT] = {};
@@ -66,7 +67,7 @@ const char* BASE_NAMES[KC_BASE_COUNT] = {
 void prof_pre(int id, cudaStream_t s) {
   g.launches++;
   if (id >= 0 && id < KC_COUNT) g.per_class_launches[id]++;
-  if (g.on && (g.target < 0 || g.target == id)) {
+  if (g.on && !g.capturing && (g.target < 0 || g.target == id)) {
     g.open_a = take_event();
     g.open_id = id;
     if (g.open_a) cudaEventRecord(g.open_a, s);
@@ -87,6 +88,10 @@ void prof_post(int id, double bytes, cudaStream_t s) {
     if (g.pending.size() >= 8192) harvest();
   }
 }
+
+void prof_add_launches(int64_t n) { g.launches += n; }
+void prof_set_capturing(bool on) { g.capturing = on; }
+int64_t prof_launches() { return g.launches; }
 
 const char* kclass_name(int id) {
   static thread_local std::string s;

@@ -24,6 +24,10 @@ inline int kclass(int base, bool fp64, bool coarse) {
 }
 
 void prof_pre(int id, cudaStream_t s);
+// launches replayed by graphs are added here; while capturing, event timing is suspended
+void prof_add_launches(int64_t n);
+void prof_set_capturing(bool on);
+int64_t prof_launches();
 void prof_post(int id, double bytes, cudaStream_t s);
 const char* kclass_name(int id);
 

@@ -95,6 +95,8 @@ Grid make_grid(const pf_mesh_desc& d, int level) {
     g.pin_x2[k] = d.pin_x2[k] / f;
     g.pin_y2[k] = d.pin_y2[k] / f;
     g.pin_comp[k] = d.pin_comp[k];
+    if (g.pin_x2[k] > 0 && g.pin_x2[k] < 2 * g.nx && g.pin_y2[k] > 0 && g.pin_y2[k] < 2 * g.ny)
+      g.interior_pins = 1;
   }
   return g;
 }
@@ -166,6 +168,8 @@ void take_level(Arena& a, Level& L, bool coarsest) {
     B.AD = a.take<T>(nd * nd);
     B.diagE = a.take<T>(ne);
     B.diagD = a.take<T>(nd);
+    B.AEi = a.take<T>(ne * ne);
+    B.ADi = a.take<T>(nd * nd);
   }
 }
 
@@ -214,6 +218,7 @@ void layout(pf_sim& s, Arena& a) {
   for (int l = 0; l < L; ++l) {
     take_level<double>(a, s.lv[l], l == L - 1);
     take_level<float>(a, s.lv[l], l == L - 1);
+    if (l > 0) s.lv[l].exclD = a.take<uint8_t>(s.lv[l].g.n);
   }
   size_t nb = ((size_t)(g.nx + 1 + TX - 1) / TX) * ((g.ny + 1 + TY - 1) / TY);
   nb = std::max<size_t>(nb, MAX_RED_BLOCKS);
@@ -269,7 +274,7 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
     DamageArgs<T> a{};
     a.x = x;
     a.w = L.buf<T>().wD;
-    a.excl = l == 0 ? s.act : nullptr;
+    a.excl = l == 0 ? s.act : L.exclD;
     a.y = y;
     a.slot = slot(s, sl);
     a.coarse = l > 0;
@@ -293,7 +298,7 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     DamageArgs<T> a{};
     a.x = x;
     a.w = L.buf<T>().wD;
-    a.excl = l == 0 ? s.act : nullptr;
+    a.excl = l == 0 ? s.act : L.exclD;
     a.b = b;
     a.y = r;
     a.coarse = l > 0;
@@ -323,7 +328,7 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     DamageArgs<T> a{};
     a.x = x;
     a.w = L.buf<T>().wD;
-    a.excl = l == 0 ? s.act : nullptr;
+    a.excl = l == 0 ? s.act : L.exclD;
     a.b = b;
     a.d = d;
     a.dinv = L.buf<T>().dinvD;
@@ -380,7 +385,7 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
   const int nlev = (int)s.lv.size();
   if (l == nlev - 1) {
     if (L.dense && nlev > 1) {
-      coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AE : B.AD, b, x);
+      coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AEi : B.ADi, b, x);
     } else {
       smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * deg : deg);
     }
@@ -390,10 +395,11 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
   LevelBuf<T>& BC = C.buf<T>();
   smooth<T>(s, st, phys, l, b, x, true, deg);
   residual_op<T>(s, st, phys, l, b, x, B.r);
-  restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b);
+  restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b,
+                  phys == DAMAGE ? C.exclD : nullptr);
   vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
   prolong_add<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, BC.x, x,
-                 (phys == DAMAGE && l == 0) ? s.act : nullptr);
+                 phys == DAMAGE ? (l == 0 ? s.act : L.exclD) : nullptr);
   smooth<T>(s, st, phys, l, b, x, false, deg);
 }
 
@@ -421,8 +427,9 @@ void setup_elastic(pf_sim& s, cudaStream_t st) {
   Level& Lc = s.lv[nlev - 1];
   if (Lc.dense && nlev > 1) {
     LevelBuf<T>& B = Lc.buf<T>();
-    coarse_assemble<T>(st, Lc.g, s.m, ELASTIC, B.coefE, B.AE, B.diagE);
+    coarse_assemble<T>(st, Lc.g, s.m, ELASTIC, B.coefE, B.AE, B.diagE, nullptr);
     coarse_factor<T>(st, 2 * Lc.g.n, B.AE, B.diagE);
+    coarse_invert<T>(st, 2 * Lc.g.n, B.AE, B.AEi);
   }
 }
 
@@ -433,18 +440,29 @@ void setup_damage(pf_sim& s, cudaStream_t st) {
     coarsen_coef<T>(st, s.lv[l - 1].g, s.lv[l].g, s.lv[l - 1].buf<T>().wD, s.lv[l].buf<T>().wD);
   for (int l = 0; l < nlev; ++l)
     l1_dinv_damage<T>(st, s.lv[l].g, s.m, s.lv[l].buf<T>().wD, s.lv[l].buf<T>().dinvD);
+}
+
+// The active set changed: coarse-level masks (a coarse node is excluded iff its coincident fine
+// node is) and the coarsest level's dense inverse of the masked operator.
+template <class T>
+void damage_masks(pf_sim& s, cudaStream_t st) {
+  const int nlev = (int)s.lv.size();
+  for (int l = 1; l < nlev; ++l)
+    mask_restrict(st, s.lv[l - 1].g, s.lv[l].g, l == 1 ? s.act : s.lv[l - 1].exclD, s.lv[l].exclD);
   Level& Lc = s.lv[nlev - 1];
   if (Lc.dense && nlev > 1) {
     LevelBuf<T>& B = Lc.buf<T>();
-    coarse_assemble<T>(st, Lc.g, s.m, DAMAGE, B.wD, B.AD, B.diagD);
+    coarse_assemble<T>(st, Lc.g, s.m, DAMAGE, B.wD, B.AD, B.diagD, Lc.exclD);
     coarse_factor<T>(st, Lc.g.n, B.AD, B.diagD);
+    coarse_invert<T>(st, Lc.g.n, B.AD, B.ADi);
   }
 }
 
 // Preconditioned CG for A_ff x = b (x starts at 0).  Stops when ||r|| <= rtol ||b||.
+// Host-driven loop: one read-back of ||r||^2 per iteration.
 template <class T>
-pf_status pcg(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, double rtol, int deg,
-              int64_t* iters, double* relres) {
+pf_status pcg_host(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, double rtol,
+                   int deg, int64_t* iters, double* relres) {
   Krylov<T>& K = kry<T>(s);
   const int nc = phys == ELASTIC ? 2 : 1;
   const size_t nd = (size_t)nc * s.lv[0].g.n;
@@ -480,6 +498,109 @@ pf_status pcg(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, doubl
   if (it > maxit) return fail(PF_ENOTCONV, "CG did not converge in %d iterations (rel. res. %.3e)",
                               maxit, sqrt(rr / rr0));
   return PF_OK;
+}
+
+// One CG iteration body, in the order: z = M r; rz_new = r.z; p = z + (rz_new/rz_old) p;
+// Ap, pAp; x += a p, r -= a Ap, rr; control (rz_old <- rz_new, loop while rr > tol2).
+template <class T>
+pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
+  const int pi = sizeof(T) == 8 ? 1 : 0;
+  if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == deg) return PF_OK;
+  if (s.cg_exec[phys][pi]) {
+    cudaGraphExecDestroy(s.cg_exec[phys][pi]);
+    cudaGraphDestroy(s.cg_graph[phys][pi]);
+    s.cg_exec[phys][pi] = nullptr;
+    s.cg_graph[phys][pi] = nullptr;
+  }
+  Krylov<T>& K = kry<T>(s);
+  const size_t nd = (size_t)(phys == ELASTIC ? 2 : 1) * s.lv[0].g.n;
+  cudaGraph_t g;
+  CU(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  prof_set_capturing(true);
+  const int64_t l0 = prof_launches();
+  precond<T>(s, cs, phys, K.r, K.z, deg);
+  vec_dot<T>(cs, K.r, K.z, nd, slot(s, S_RZ1));
+  cg_update_p<T>(cs, K.p, K.z, nd, s.scal + S_RZ1, s.scal + S_RZ0);
+  apply_op<T>(s, cs, phys, 0, K.p, K.Ap, true, S_PAP);
+  cg_update_xr<T>(cs, K.x, K.r, K.p, K.Ap, nd, s.scal + S_RZ1, s.scal + S_PAP, slot(s, S_RR));
+  cg_control(cs, h, s.scal + S_RZ1, s.scal + S_RZ0, s.scal + S_RR, s.scal + S_TOL2, s.scal + S_IT,
+             s.scal + S_MAXIT);
+  const int64_t nk = prof_launches() - l0;
+  prof_add_launches(-nk);  // counted again each time the graph replays them
+  prof_set_capturing(false);
+  cudaGraph_t captured;
+  cudaError_t e1 = cudaStreamEndCapture(cs, &captured);
+  cudaError_t e2 = cudaStreamDestroy(cs);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(PF_ECUDA, "CG graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+  }
+  cudaGraphExec_t ex;
+  cudaError_t e3 = cudaGraphInstantiate(&ex, g, 0);
+  if (e3 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(PF_ECUDA, "CG graph instantiation failed: %s", cudaGetErrorString(e3));
+  }
+  s.cg_graph[phys][pi] = g;
+  s.cg_exec[phys][pi] = ex;
+  s.cg_body_kernels[phys][pi] = (int)nk;
+  s.cg_deg[phys][pi] = deg;
+  return PF_OK;
+}
+
+// Same solve as pcg_host with the whole iteration loop inside one CUDA graph launch.
+template <class T>
+pf_status pcg_graph(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, double rtol,
+                    int deg, int64_t* iters, double* relres) {
+  Krylov<T>& K = kry<T>(s);
+  const size_t nd = (size_t)(phys == ELASTIC ? 2 : 1) * s.lv[0].g.n;
+  const int pi = sizeof(T) == 8 ? 1 : 0;
+  TRY(build_cg_graph<T>(s, phys, deg));
+  vec_fill<T>(st, K.x, T(0), nd);
+  CU(cudaMemcpyAsync(K.r, b, nd * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  vec_dot<T>(st, K.r, K.r, nd, slot(s, S_RR));
+  double rr0;
+  TRY(read_scalars(s, st, S_RR, 1, &rr0));
+  if (!(rr0 == rr0) || isinf(rr0)) return fail(PF_ENUMERIC, "CG: right-hand side is not finite");
+  if (relres) *relres = 0.0;
+  if (rr0 == 0.0) return PF_OK;
+  const double tol2 = rtol * rtol * rr0;
+  double* hb = s.ctx->host;
+  hb[0] = tol2;
+  hb[1] = 0.0;
+  hb[2] = double(maxit);
+  CU(cudaMemcpyAsync(s.scal + S_TOL2, hb, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(s.scal + S_RZ0, 0, sizeof(double), st));
+  CU(cudaGraphLaunch(s.cg_exec[phys][pi], st));
+  double rr, it;
+  TRY(read_scalars(s, st, S_RR, 1, &rr));
+  TRY(read_scalars(s, st, S_IT, 1, &it));
+  prof_add_launches((int64_t)it * s.cg_body_kernels[phys][pi]);
+  if (!(rr == rr)) return fail(PF_ENUMERIC, "CG breakdown (NaN residual)");
+  if (iters) *iters += (int64_t)it;
+  if (relres) *relres = sqrt(rr / rr0);
+  if (rr > tol2) return fail(PF_ENOTCONV, "CG did not converge in %d iterations (rel. res. %.3e)",
+                             maxit, sqrt(rr / rr0));
+  return PF_OK;
+}
+
+template <class T>
+pf_status pcg(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, double rtol, int deg,
+              int64_t* iters, double* relres) {
+  if (s.use_graphs) return pcg_graph<T>(s, st, phys, b, maxit, rtol, deg, iters, relres);
+  return pcg_host<T>(s, st, phys, b, maxit, rtol, deg, iters, relres);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -630,6 +751,8 @@ pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_st
                                       it, phi, tol);
     ++it;
     // reduced Newton step on the inactive set: H_NN d_N = -F_N, d_A = 0 (eq. reducednewton)
+    if (mixed) damage_masks<float>(s, st);
+    else damage_masks<double>(s, st);
     if (!mixed) {
       pf_status stt = pcg<double>(s, st, DAMAGE, s.rhs, o.cg_maxit, o.alpha_cg_rtol, o.mg_degree,
                                   rep ? &rep->cg_iters_alpha : nullptr, nullptr);
@@ -662,7 +785,8 @@ pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_st
           std::swap(s.F, s.Ftr);
           std::swap(s.Phi, s.Phitr);
           std::swap(s.rhs, s.rhstr);
-          std::swap(s.act, s.acttr);
+          // the active flags stay in place: CUDA graphs of the damage PCG read this buffer
+          CU(cudaMemcpyAsync(s.act, s.acttr, n, cudaMemcpyDeviceToDevice, st));
           phi2 = w[0];
           accepted = true;
           break;
@@ -820,7 +944,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->newton_maxit = 30;
   o->minres_maxit = 500;
   o->minres_rtol = 1e-6;
-  o->use_graphs = 0;
+  o->use_graphs = 1;
   return PF_OK;
 }
 
@@ -966,6 +1090,7 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   CU(cudaSetDevice(s->ctx->device));
   s->busy = true;
   auto t0 = std::chrono::steady_clock::now();
+  s->use_graphs = o->use_graphs != 0;
   pf_step_report r{};
   r.omega_bar_min = o->omega;
   pf_status status = begin_step(*s, st, *L);
@@ -1128,6 +1253,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   s->r_scale = 0.0;
+  s->use_graphs = o->use_graphs != 0;
   s->elastic_ready64 = s->elastic_ready32 = false;
   pf_step_report r{};
   pf_status status = u_solve(*s, st, *o, &r);
@@ -1146,6 +1272,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   s->phi_scale = 0.0;
+  s->use_graphs = o->use_graphs != 0;
   pf_step_report r{};
   pf_status status = alpha_solve(*s, st, *o, &r);
   if (status == PF_OK || status == PF_ENOTCONV) {

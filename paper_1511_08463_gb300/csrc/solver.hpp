@@ -22,6 +22,7 @@ struct LevelBuf {
   T* dinvD = nullptr;   // (n)
   T *b = nullptr, *x = nullptr, *r = nullptr, *xt = nullptr, *d = nullptr, *dt = nullptr;  // 2n
   T *AE = nullptr, *AD = nullptr, *diagE = nullptr, *diagD = nullptr;  // coarsest dense
+  T *AEi = nullptr, *ADi = nullptr;  // coarsest explicit inverses
 };
 
 struct Level {
@@ -29,6 +30,7 @@ struct Level {
   LevelBuf<double> f64;
   LevelBuf<float> f32;
   bool dense = false;  // coarsest level solved by dense Cholesky
+  uint8_t* exclD = nullptr;  // damage: active-set mask of this coarse level (level 0 uses the sim's)
   template <class T>
   LevelBuf<T>& buf();
 };
@@ -47,7 +49,7 @@ enum Slot {
   S_RR = 0, S_RZ0 = 1, S_RZ1 = 2, S_PAP = 3, S_RES = 4, S_DU = 5,   // S_DU: 2 values
   S_OMEGA = 8, S_DALPHA = 9, S_PHI = 10,                            // S_PHI: 2 values
   S_EN = 12,                                                         // 2 values
-  S_TMP = 16, S_COUNT = 32
+  S_TMP = 16, S_TOL2 = 20, S_IT = 21, S_MAXIT = 22, S_COUNT = 32
 };
 
 // shared with other translation units of the library
@@ -90,4 +92,18 @@ struct pf_sim {
        damage_ready32 = false;
   size_t ws_used = 0;
   bool busy = false;
+  // CUDA graphs holding one whole PCG solve each (device-side while loop), per operator
+  // (elastic, damage) and precision (FP32, FP64); rebuilt if the smoothing degree changes
+  bool use_graphs = true;
+  cudaGraph_t cg_graph[2][2] = {};
+  cudaGraphExec_t cg_exec[2][2] = {};
+  int cg_body_kernels[2][2] = {};
+  int cg_deg[2][2] = {};
+  ~pf_sim() {
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        if (cg_exec[a][b]) cudaGraphExecDestroy(cg_exec[a][b]);
+        if (cg_graph[a][b]) cudaGraphDestroy(cg_graph[a][b]);
+      }
+  }
 };

@@ -28,10 +28,17 @@ enum Mode : int {
   M_TRIAL = 6    // damage: same as M_GRAD at x_t = clip(x + mu d, lo, hi); writes x_t
 };
 
+// Kernel constants in the operator's own precision, prepared on the host so that FP32 kernels
+// perform no per-element FP64 conversions (FP64 throughput is ~1/58 of FP32 on this part).
 template <class T>
-struct V2 {
-  T x, y;
+struct Consts {
+  T ihx, ihy, area, lam, mu, lam2mu, k_ell, c1, c2, c3;
 };
+template <class T>
+inline Consts<T> make_consts(const Grid& g, const Mat& m) {
+  return Consts<T>{T(g.ihx), T(g.ihy), T(g.area), T(m.lam), T(m.mu), T(m.lam2mu), T(m.k_ell),
+                   T(m.c1), T(m.c2), T(m.c3)};
+}
 
 // ----------------------------------------------------------------------------------------------
 // generic tile kernel
@@ -40,12 +47,16 @@ template <class Op>
 __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
   using V = typename Op::V;
   using R = typename Op::R;
+  using ET = typename Op::ET;
   constexpr int KIND = Op::KIND;
   constexpr int NE = elems_per_cell(KIND);
+  constexpr int NRC = Op::NRC;
   constexpr int NC = KIND == CROSSED ? TY + 1 : 1;
   __shared__ V sv[TY + 2][TX + 2];
   __shared__ V sc[NC][TX + 1];
-  __shared__ R se[TY + 1][TX + 1][NE];
+  // element records stored component-major: consecutive cells -> consecutive words, so both the
+  // record writes and the gathers are free of shared-memory bank conflicts
+  __shared__ ET se[NRC][NE][TY + 1][TX + 1];
   const Grid& g = op.g;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -66,6 +77,10 @@ __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
     }
   }
   __syncthreads();
+  auto put = [&](int t, int lj, int li, const R& r) {
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) se[c][t][lj][li] = r.c[c];
+  };
   for (int s = tid; s < (TX + 1) * (TY + 1); s += TX * TY) {
     int li = s % (TX + 1), lj = s / (TX + 1);
     int ci = i0 - 1 + li, cj = j0 - 1 + lj;
@@ -74,55 +89,62 @@ __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
     int cell = cj * g.nx + ci;
     if constexpr (KIND == CROSSED) {
       V c = sc[lj][li];
-      se[lj][li][0] = op.template element<0>(valid, cell, cj, v00, v10, c);
-      se[lj][li][1] = op.template element<1>(valid, cell, cj, v10, v11, c);
-      se[lj][li][2] = op.template element<2>(valid, cell, cj, v11, v01, c);
-      se[lj][li][3] = op.template element<3>(valid, cell, cj, v01, v00, c);
+      put(0, lj, li, op.template element<0>(valid, cell, cj, v00, v10, c));
+      put(1, lj, li, op.template element<1>(valid, cell, cj, v10, v11, c));
+      put(2, lj, li, op.template element<2>(valid, cell, cj, v11, v01, c));
+      put(3, lj, li, op.template element<3>(valid, cell, cj, v01, v00, c));
     } else {
-      se[lj][li][0] = op.template element<0>(valid, cell, cj, v00, v10, v11);
-      se[lj][li][1] = op.template element<1>(valid, cell, cj, v00, v11, v01);
+      put(0, lj, li, op.template element<0>(valid, cell, cj, v00, v10, v11));
+      put(1, lj, li, op.template element<1>(valid, cell, cj, v00, v11, v01));
     }
   }
   __syncthreads();
+  auto get = [&](int t, int lj, int li) {
+    R r;
+#pragma unroll
+    for (int c = 0; c < NRC; ++c) r.c[c] = se[c][t][lj][li];
+    return r;
+  };
 
   constexpr int NRA = Op::NR > 0 ? Op::NR : 1;
-  double red[NRA];
+  using RT = typename Op::RT;
+  RT red[NRA];
 #pragma unroll
-  for (int q = 0; q < NRA; ++q) red[q] = Op::RED_MAX ? -INFINITY : 0.0;
+  for (int q = 0; q < NRA; ++q) red[q] = RT(0);
 
   const int i = i0 + tx, j = j0 + ty;
   if (i <= g.nx && j <= g.ny) {
     typename Op::Acc a = Op::acc0();
     if constexpr (KIND == CROSSED) {
-      op.template add<0, 0>(a, se[ty + 1][tx + 1][0]);  // cell (i, j): vertex is v00
-      op.template add<3, 1>(a, se[ty + 1][tx + 1][3]);
-      op.template add<0, 1>(a, se[ty + 1][tx][0]);      // cell (i-1, j): v10
-      op.template add<1, 0>(a, se[ty + 1][tx][1]);
-      op.template add<1, 1>(a, se[ty][tx][1]);          // cell (i-1, j-1): v11
-      op.template add<2, 0>(a, se[ty][tx][2]);
-      op.template add<2, 1>(a, se[ty][tx + 1][2]);      // cell (i, j-1): v01
-      op.template add<3, 0>(a, se[ty][tx + 1][3]);
+      op.template add<0, 0>(a, get(0, ty + 1, tx + 1));  // cell (i, j): vertex is v00
+      op.template add<3, 1>(a, get(3, ty + 1, tx + 1));
+      op.template add<0, 1>(a, get(0, ty + 1, tx));      // cell (i-1, j): v10
+      op.template add<1, 0>(a, get(1, ty + 1, tx));
+      op.template add<1, 1>(a, get(1, ty, tx));          // cell (i-1, j-1): v11
+      op.template add<2, 0>(a, get(2, ty, tx));
+      op.template add<2, 1>(a, get(2, ty, tx + 1));      // cell (i, j-1): v01
+      op.template add<3, 0>(a, get(3, ty, tx + 1));
     } else {
-      op.template add<0, 0>(a, se[ty + 1][tx + 1][0]);  // cell (i, j): v00
-      op.template add<1, 0>(a, se[ty + 1][tx + 1][1]);
-      op.template add<0, 1>(a, se[ty + 1][tx][0]);      // cell (i-1, j): v10
-      op.template add<0, 2>(a, se[ty][tx][0]);          // cell (i-1, j-1): v11
-      op.template add<1, 1>(a, se[ty][tx][1]);
-      op.template add<1, 2>(a, se[ty][tx + 1][1]);      // cell (i, j-1): v01
+      op.template add<0, 0>(a, get(0, ty + 1, tx + 1));  // cell (i, j): v00
+      op.template add<1, 0>(a, get(1, ty + 1, tx + 1));
+      op.template add<0, 1>(a, get(0, ty + 1, tx));      // cell (i-1, j): v10
+      op.template add<0, 2>(a, get(0, ty, tx));          // cell (i-1, j-1): v11
+      op.template add<1, 1>(a, get(1, ty, tx));
+      op.template add<1, 2>(a, get(1, ty, tx + 1));      // cell (i, j-1): v01
     }
     op.store(j * (g.nx + 1) + i, 2 * i, 2 * j, sv[ty + 1][tx + 1], a, red);
   }
   if constexpr (KIND == CROSSED) {
     if (i < g.nx && j < g.ny) {
       typename Op::Acc a = Op::acc0();
-      op.template add<0, 2>(a, se[ty + 1][tx + 1][0]);
-      op.template add<1, 2>(a, se[ty + 1][tx + 1][1]);
-      op.template add<2, 2>(a, se[ty + 1][tx + 1][2]);
-      op.template add<3, 2>(a, se[ty + 1][tx + 1][3]);
+      op.template add<0, 2>(a, get(0, ty + 1, tx + 1));
+      op.template add<1, 2>(a, get(1, ty + 1, tx + 1));
+      op.template add<2, 2>(a, get(2, ty + 1, tx + 1));
+      op.template add<3, 2>(a, get(3, ty + 1, tx + 1));
       op.store(g.nv + j * g.nx + i, 2 * i + 1, 2 * j + 1, sc[ty + 1][tx + 1], a, red);
     }
   }
-  if constexpr (Op::NR > 0) block_reduce_finalize<Op::NR, Op::RED_MAX>(red, op.args.slot);
+  if constexpr (Op::NR > 0) block_reduce_finalize<Op::NR, Op::RED_MAX, RT>(red, op.args.slot);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -152,17 +174,21 @@ struct ElasticOp {
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
   static constexpr bool RED_MAX = false;
+  using RT = T;  // per-thread partial sums in the operator's precision
   struct V {
     T ux, uy, a;
   };
+  using ET = T;
+  static constexpr int NRC = 3;
   struct R {
-    T sxx, syy, sxy;
+    T c[3];  // w A0 eps: sxx, syy, sxy
   };
   struct Acc {
     T ax, bx, ay, by;
   };
   Grid g;
   Mat m;
+  Consts<T> cs;
   ElasticArgs<T> args;
 
   __device__ static V zero() { return V{T(0), T(0), T(0)}; }
@@ -182,14 +208,14 @@ struct ElasticOp {
 
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
-    if (!valid) return R{T(0), T(0), T(0)};
+    if (!valid) return R{{T(0), T(0), T(0)}};
     constexpr int NE = elems_per_cell(KIND);
     T w;
     if (COEF == COEF_ALPHA)
-      w = abar3<T>(n0.a, n1.a, n2.a, T(m.k_ell)) * T(g.area);
+      w = abar3<T>(n0.a, n1.a, n2.a, cs.k_ell) * cs.area;
     else
-      w = args.coef[cell * NE + t] * T(g.area);
-    T ihx = T(g.ihx), ihy = T(g.ihy);
+      w = args.coef[cell * NE + t] * cs.area;
+    const T ihx = cs.ihx, ihy = cs.ihy;
     T sx = T(gx(KIND, t, 0)) * n0.ux + T(gx(KIND, t, 1)) * n1.ux + T(gx(KIND, t, 2)) * n2.ux;
     T sy = T(gy(KIND, t, 0)) * n0.uy + T(gy(KIND, t, 1)) * n1.uy + T(gy(KIND, t, 2)) * n2.uy;
     T s1 = T(gy(KIND, t, 0)) * n0.ux + T(gy(KIND, t, 1)) * n1.ux + T(gy(KIND, t, 2)) * n2.ux;
@@ -200,27 +226,27 @@ struct ElasticOp {
       exx -= e0;
       eyy -= e0;
     }
-    T lam = T(m.lam), l2m = T(m.lam2mu), mu = T(m.mu);
-    return R{w * (l2m * exx + lam * eyy), w * (lam * exx + l2m * eyy), w * mu * gxy};
+    const T lam = cs.lam, l2m = cs.lam2mu, mu = cs.mu;
+    return R{{w * (l2m * exx + lam * eyy), w * (lam * exx + l2m * eyy), w * mu * gxy}};
   }
 
   template <int t, int k>
   __device__ void add(Acc& a, const R& r) const {
     constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
     if (cx != 0) {
-      a.ax += T(cx) * r.sxx;
-      a.ay += T(cx) * r.sxy;
+      a.ax += T(cx) * r.c[0];
+      a.ay += T(cx) * r.c[2];
     }
     if (cy != 0) {
-      a.bx += T(cy) * r.sxy;
-      a.by += T(cy) * r.syy;
+      a.bx += T(cy) * r.c[2];
+      a.by += T(cy) * r.c[1];
     }
   }
 
   __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
-                        double (&red)[NR > 0 ? NR : 1]) const {
-    T fx = T(g.ihx) * a.ax + T(g.ihy) * a.bx;
-    T fy = T(g.ihx) * a.ay + T(g.ihy) * a.by;
+                        RT (&red)[NR > 0 ? NR : 1]) const {
+    T fx = cs.ihx * a.ax + cs.ihy * a.bx;
+    T fy = cs.ihx * a.ay + cs.ihy * a.by;
     bool f0 = false, f1 = false;
     if (MODE != M_APPLY) {
       f0 = is_fixed(g, X2, Y2, 0);
@@ -230,17 +256,17 @@ struct ElasticOp {
       T yx = f0 ? T(0) : fx, yy = f1 ? T(0) : fy;
       args.y[2 * node] = yx;
       args.y[2 * node + 1] = yy;
-      if (DOT) red[0] += double(own.ux) * double(yx) + double(own.uy) * double(yy);
+      if (DOT) red[0] += own.ux * yx + own.uy * yy;
     } else if (MODE == M_RESB) {
       T rx = f0 ? T(0) : args.b[2 * node] - fx, ry = f1 ? T(0) : args.b[2 * node + 1] - fy;
       args.y[2 * node] = rx;
       args.y[2 * node + 1] = ry;
-      if (DOT) red[0] += double(rx) * double(rx) + double(ry) * double(ry);
+      if (DOT) red[0] += rx * rx + ry * ry;
     } else if (MODE == M_RESID) {
       T rx = f0 ? T(0) : -fx, ry = f1 ? T(0) : -fy;
       args.y[2 * node] = rx;
       args.y[2 * node + 1] = ry;
-      red[0] += double(rx) * double(rx) + double(ry) * double(ry);
+      red[0] += rx * rx + ry * ry;
     } else if (MODE == M_CHEB) {
       T rx = args.b[2 * node] - fx, ry = args.b[2 * node + 1] - fy;
       T px = args.d ? args.d[2 * node] : T(0), py = args.d ? args.d[2 * node + 1] : T(0);
@@ -282,17 +308,21 @@ struct DamageOp {
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
   static constexpr bool RED_MAX = false;
+  using RT = T;
   struct V {
     T p;
   };
+  using ET = T;
+  static constexpr int NRC = 4;
   struct R {
-    T P, M, X, Y;
+    T c[4];  // P, M, X, Y
   };
   struct Acc {
     T P, M, X, Y;
   };
   Grid g;
   Mat m;
+  Consts<T> cs;
   DamageArgs<T> args;
 
   __device__ static V zero() { return V{T(0)}; }
@@ -317,45 +347,45 @@ struct DamageOp {
 
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
-    if (!valid) return R{T(0), T(0), T(0), T(0)};
+    if (!valid) return R{{T(0), T(0), T(0), T(0)}};
     constexpr int NE = elems_per_cell(KIND);
-    T area = T(g.area);
+    const T area = cs.area;
     T wt = args.w[cell * NE + t];
     T qT = wt;
-    if (MODE == M_GRAD || MODE == M_TRIAL) wt = wt + T(m.c2);
+    if (MODE == M_GRAD || MODE == M_TRIAL) wt = wt + cs.c2;
     T me = wt * area * T(1.0 / 12.0);
     T S = n0.p + n1.p + n2.p;
-    T gpx = T(g.ihx) * (T(gx(KIND, t, 0)) * n0.p + T(gx(KIND, t, 1)) * n1.p + T(gx(KIND, t, 2)) * n2.p);
-    T gpy = T(g.ihy) * (T(gy(KIND, t, 0)) * n0.p + T(gy(KIND, t, 1)) * n1.p + T(gy(KIND, t, 2)) * n2.p);
-    T c1a = T(m.c1) * area;
+    T gpx = cs.ihx * (T(gx(KIND, t, 0)) * n0.p + T(gx(KIND, t, 1)) * n1.p + T(gx(KIND, t, 2)) * n2.p);
+    T gpy = cs.ihy * (T(gy(KIND, t, 0)) * n0.p + T(gy(KIND, t, 1)) * n1.p + T(gy(KIND, t, 2)) * n2.p);
+    T c1a = cs.c1 * area;
     T P = me * S;
-    if (MODE == M_GRAD || MODE == M_TRIAL) P += (T(m.c3) - qT) * area * T(1.0 / 3.0);
-    return R{P, me, c1a * T(g.ihx) * gpx, c1a * T(g.ihy) * gpy};
+    if (MODE == M_GRAD || MODE == M_TRIAL) P += (cs.c3 - qT) * area * T(1.0 / 3.0);
+    return R{{P, me, c1a * cs.ihx * gpx, c1a * cs.ihy * gpy}};
   }
 
   template <int t, int k>
   __device__ void add(Acc& a, const R& r) const {
     constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
-    a.P += r.P;
-    a.M += r.M;
-    if (cx != 0) a.X += T(cx) * r.X;
-    if (cy != 0) a.Y += T(cy) * r.Y;
+    a.P += r.c[0];
+    a.M += r.c[1];
+    if (cx != 0) a.X += T(cx) * r.c[2];
+    if (cy != 0) a.Y += T(cy) * r.c[3];
   }
 
   __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
-                        double (&red)[NR > 0 ? NR : 1]) const {
+                        RT (&red)[NR > 0 ? NR : 1]) const {
     T f = a.P + a.M * own.p + a.X + a.Y;
     if (MODE == M_APPLY) {
       args.y[node] = f;
-      if (DOT) red[0] += double(own.p) * double(f);
+      if (DOT) red[0] += own.p * f;
     } else if (MODE == M_MASKED) {
       T v = (args.excl && args.excl[node]) ? T(0) : f;
       args.y[node] = v;
-      if (DOT) red[0] += double(own.p) * double(v);
+      if (DOT) red[0] += own.p * v;
     } else if (MODE == M_RESB) {
       T r = (args.excl && args.excl[node]) ? T(0) : args.b[node] - f;
       args.y[node] = r;
-      if (DOT) red[0] += double(r) * double(r);
+      if (DOT) red[0] += r * r;
     } else if (MODE == M_CHEB) {
       T dp = args.d ? args.d[node] : T(0);
       T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
@@ -371,8 +401,8 @@ struct DamageOp {
       args.rhs[node] = active ? T(0) : T(-F);
       args.act[node] = active ? 1 : 0;
       if (MODE == M_TRIAL) args.xt[node] = own.p;
-      red[0] += ph * ph;
-      red[1] += active ? 0.0 : F * F;
+      red[0] += T(ph * ph);
+      red[1] += active ? T(0) : T(F * F);
     }
   }
 };

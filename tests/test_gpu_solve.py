@@ -138,3 +138,22 @@ def test_single_level_and_jacobi_paths():
     for rep, r in reps:
         np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
     _fields_close(g, p)
+
+
+def test_graph_and_host_loops_agree_bitwise():
+    """The CUDA-graph PCG (device-side loop) runs the same kernels in the same order as the
+    host-driven loop, so the load steps agree bit for bit."""
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    w = W.notched_square(n=32, n_steps=10, t_max=1.0)
+    out = []
+    for graphs in (0, 1):
+        g = S.Sim(w)
+        opts = tight_opts(S, omega=1.5, precision="mixed", use_graphs=graphs)
+        reps = [g.load_step(t, dT, opts) for (t, dT) in w.loads[:4]]
+        out.append((g.get_fields(), reps))
+    for a, b in zip(out[0][0], out[1][0]):
+        np.testing.assert_array_equal(a, b)
+    for ra, rb in zip(out[0][1], out[1][1]):
+        assert ra["cg_iters_u"] == rb["cg_iters_u"] and ra["cg_iters_alpha"] == rb["cg_iters_alpha"]
