@@ -419,6 +419,7 @@ def run_ours(args):
                        "cg_u": sum(r["cg_iters_u"] for r in reps),
                        "cg_alpha": sum(r["cg_iters_alpha"] for r in reps),
                        "rs_iters": sum(r["rs_iters"] for r in reps),
+                       "u_solves_reused": sum(r["u_solves_reused"] for r in reps),
                        "not_converged_steps": sum(1 for r in reps if r["status"] != 0),
                        "final_energy": reps[-1]["energy"]},
             "kernel_classes_replay_step": {k: {"ms": round(v["ms"], 3),

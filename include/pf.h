@@ -133,6 +133,8 @@ typedef struct pf_step_report {
   double dalpha_inf, du_rel, phi_norm, phi_start, omega_bar_min;
   double energy[3]; /* elastic, surface, total */
   double seconds;
+  int64_t u_solves_reused; /* AM iterations whose u-subproblem had the same alpha and load as the
+                              previous one, so its minimizer was reused instead of re-solved */
 } pf_step_report;
 
 typedef struct pf_ctx pf_ctx;

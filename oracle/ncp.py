@@ -13,7 +13,9 @@ Components without bounds (displacements) use Phi_i = F_i.
 
 Algorithm 4 (reduced-space active set): active set A = {x_i <= l_i + zeta and F_i > 0} union
 {x_i >= u_i - zeta and F_i < 0} (eq. reducedis, both bounds), plus every component whose box is a
-single point; d_A = 0; solve J_NN d_N = -F_N (eq. reducednewton); line search on ||Phi||^2 over
+single point; zeta being the zero tolerance, active components are taken to lie on their bound
+and the step moves them onto it exactly (the paper's d_A = 0 up to that tolerance); solve
+J_NN d_N = -F_N (eq. reducednewton); line search on ||Phi||^2 over
 projected points pi[x + mu d], mu = 1, 1/2, ..., 2^-20, Armijo constant 1e-4; if it fails, the
 steepest-descent direction of ||Phi||^2/2 is tried with the same search.
 
@@ -49,12 +51,20 @@ def mcp_residual(x, F, lo, hi, bounded):
     return Phi
 
 
-def active_set(x, F, lo, hi, bounded, zeta):
-    act = np.zeros(x.shape, dtype=bool)
+def active_sets(x, F, lo, hi, bounded, zeta):
+    """(lower-active, upper-active) index masks of eq. reducedis with both bounds; a box that is
+    a single point counts as lower-active."""
+    low = np.zeros(x.shape, dtype=bool)
+    up = np.zeros(x.shape, dtype=bool)
     b = bounded
-    act[b] = ((x[b] <= lo[b] + zeta) & (F[b] > 0)) | ((x[b] >= hi[b] - zeta) & (F[b] < 0)) | \
-             (hi[b] - lo[b] <= zeta)
-    return act
+    low[b] = ((x[b] <= lo[b] + zeta) & (F[b] > 0)) | (hi[b] - lo[b] <= zeta)
+    up[b] = ~low[b] & (x[b] >= hi[b] - zeta) & (F[b] < 0)
+    return low, up
+
+
+def active_set(x, F, lo, hi, bounded, zeta):
+    low, up = active_sets(x, F, lo, hi, bounded, zeta)
+    return low | up
 
 
 def _merit_gradient(x, F, J, lo, hi, bounded):
@@ -96,13 +106,16 @@ def rs_solve(F, J, x0, lo, hi, bounded, zeta=1e-10, atol=0.0, rtol=1e-12, maxit=
             status = "maxit"
             break
         its += 1
-        act = active_set(x, Fx, lo, hi, bounded, zeta)
-        N = ~act
+        low, up = active_sets(x, Fx, lo, hi, bounded, zeta)
+        N = ~(low | up)
         Jx = J(x).tocsr()
         d = np.zeros_like(x)
         if np.any(N):
             idx = np.nonzero(N)[0]
             d[idx] = linsolve(Jx[idx][:, idx], -Fx[idx])
+        # active components lie within the zero tolerance of their bound: the step puts them on it
+        d[low] = lo[low] - x[low]
+        d[up] = hi[up] - x[up]
         m0 = float(Phi @ Phi)
         accepted = False
         for direction in ("newton", "steepest"):

@@ -58,7 +58,7 @@ class pf_step_report(C.Structure):
                 ("outer_refinements", C.c_int64), ("dalpha_inf", C.c_double),
                 ("du_rel", C.c_double), ("phi_norm", C.c_double), ("phi_start", C.c_double),
                 ("omega_bar_min", C.c_double), ("energy", C.c_double * 3),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("u_solves_reused", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

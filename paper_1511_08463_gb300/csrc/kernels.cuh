@@ -102,6 +102,9 @@ void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x);  // x
 // steepest-descent fallback of Algorithm 4: v = -pb qb Phi, dg = (pa - pb qa) Phi
 void merit_parts(cudaStream_t s, const Grid& g, const double* x, const double* F,
                  const double* lo, double* v, double* dg);
+// d_i = bound_i - x_i on active components (act 1: lower, 2: upper); other entries unchanged
+void snap_active(cudaStream_t s, const Grid& g, const uint8_t* act, const double* x, const double* lo,
+                 double* d);
 // d = -(dg + Hv)
 void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d);
 

@@ -774,6 +774,21 @@ void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x) {
 template void coarse_solve<double>(cudaStream_t, int, const double*, const double*, double*);
 template void coarse_solve<float>(cudaStream_t, int, const float*, const float*, float*);
 
+// Active components are within the zero tolerance of their bound (eq. reducedis): the step puts
+// them on it, d_i = bound_i - x_i; inactive components keep the reduced Newton step.
+__global__ void k_snap_active(Grid g, const uint8_t* act, const double* x, const double* lo, double* d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const uint8_t a = act[i];
+  if (a == 1) d[i] = lo[i] - x[i];
+  else if (a == 2) d[i] = upper_of(g, i, lo[i]) - x[i];
+}
+void snap_active(cudaStream_t s, const Grid& g, const uint8_t* act, const double* x, const double* lo,
+                 double* d) {
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s,
+            k_snap_active<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, act, x, lo, d));
+}
+
 // ---------------------------------------------------------------------------------------------
 // steepest-descent direction of ||Phi||^2 / 2 (Algorithm 4 fallback)
 // Phi_i = phi(x - l, psi), psi = phi(h - x, -F): dPhi/dx = pa - pb qa on the diagonal and

@@ -2,6 +2,7 @@
 // solve (Algorithm 4), over-relaxed alternate minimization (Algorithms 1-2) and the C ABI.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -30,6 +31,11 @@ static pf_status fail(pf_status st, const char* fmt, ...) {
 namespace pf {
 void set_error_message(const char* msg) { g_err = msg; }
 }  // namespace pf
+// PF_DEBUG=1 in the environment prints one line per damage-solve iteration on stderr
+static bool debug_enabled() {
+  static const bool on = getenv("PF_DEBUG") && getenv("PF_DEBUG")[0] == '1';
+  return on;
+}
 #define CU(call)                                                                       \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
@@ -624,7 +630,7 @@ pf_status set_load(pf_sim& s, double t, double dT, cudaStream_t st) {
     CU(cudaStreamSynchronize(st));
   }
   CU(cudaGetLastError());
-  s.elastic_ready64 = s.elastic_ready32 = false;
+  s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
   return PF_OK;
 }
 
@@ -672,7 +678,9 @@ pf_status u_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_r
       vec_add<double>(st, s.xu, s.k64.x, n2);
     } else {
       vec_convert<float, double>(st, s.tmp32, s.r64, n2);
-      pf_status stt = pcg<float>(s, st, ELASTIC, s.tmp32, o.cg_maxit, o.inner_rtol, o.mg_degree,
+      // do not reduce the residual further than the outer target needs
+      const double rel = std::min(0.5, std::max(o.inner_rtol, 0.5 * tol / rn));
+      pf_status stt = pcg<float>(s, st, ELASTIC, s.tmp32, o.cg_maxit, rel, o.mg_degree,
                                  rep ? &rep->cg_iters_u : nullptr, nullptr);
       if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
       vec_add_f32_to_f64(st, s.xu, s.k32.x, n2);
@@ -747,24 +755,31 @@ pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_st
     double phi = sqrt(phi2);
     if (!(phi == phi)) return fail(PF_ENUMERIC, "damage residual is NaN");
     if (phi <= tol || phi2 == 0.0) break;
-    if (it >= o.rs_maxit) return fail(PF_ENOTCONV, "damage solve: %d iterations, ||Phi|| %.3e > %.3e",
-                                      it, phi, tol);
+    if (it >= o.rs_maxit) {
+      if (rep) rep->rs_iters += it;
+      return fail(PF_ENOTCONV, "damage solve: %d iterations, ||Phi|| %.3e > %.3e", it, phi, tol);
+    }
     ++it;
     // reduced Newton step on the inactive set: H_NN d_N = -F_N, d_A = 0 (eq. reducednewton)
     if (mixed) damage_masks<float>(s, st);
     else damage_masks<double>(s, st);
+    // inexact Newton: solve only as accurately as the termination test of Algorithm 4 needs
+    const double cg_rel = std::min(0.5, std::max(o.alpha_cg_rtol, 0.5 * tol / phi));
+    int64_t cg_its = 0;
+    double cg_res = 0.0;
     if (!mixed) {
-      pf_status stt = pcg<double>(s, st, DAMAGE, s.rhs, o.cg_maxit, o.alpha_cg_rtol, o.mg_degree,
-                                  rep ? &rep->cg_iters_alpha : nullptr, nullptr);
+      pf_status stt = pcg<double>(s, st, DAMAGE, s.rhs, o.cg_maxit, cg_rel, o.mg_degree,
+                                  &cg_its, &cg_res);
       if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
       CU(cudaMemcpyAsync(s.drs, s.k64.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
       vec_convert<float, double>(st, s.tmp32, s.rhs, n);
-      pf_status stt = pcg<float>(s, st, DAMAGE, s.tmp32, o.cg_maxit, o.alpha_cg_rtol, o.mg_degree,
-                                 rep ? &rep->cg_iters_alpha : nullptr, nullptr);
+      pf_status stt = pcg<float>(s, st, DAMAGE, s.tmp32, o.cg_maxit, cg_rel, o.mg_degree,
+                                 &cg_its, &cg_res);
       if (stt != PF_OK && stt != PF_ENOTCONV) return stt;
       vec_convert<double, float>(st, s.drs, s.k32.x, n);
     }
+    snap_active(st, g, s.act, s.xrs, s.alpha_prev, s.drs);
     // projected line search on ||Phi||^2; steepest descent of the merit function if it fails
     bool accepted = false;
     for (int dir = 0; dir < 2 && !accepted; ++dir) {
@@ -788,12 +803,21 @@ pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_st
           // the active flags stay in place: CUDA graphs of the damage PCG read this buffer
           CU(cudaMemcpyAsync(s.act, s.acttr, n, cudaMemcpyDeviceToDevice, st));
           phi2 = w[0];
+          v[1] = w[1];
           accepted = true;
           break;
         }
       }
     }
-    if (!accepted) return fail(PF_ENOTCONV, "damage solve: line search failed at ||Phi|| %.3e", phi);
+    if (rep) rep->cg_iters_alpha += cg_its;
+    if (debug_enabled())
+      fprintf(stderr, "[pf] rs %d phi %.4e -> %.4e tol %.2e |F_N| %.3e cg %lld (rel %.1e, reached %.1e) %s\n",
+              it, phi, sqrt(phi2), tol, sqrt(v[1]), (long long)cg_its, cg_rel, cg_res,
+              accepted ? "accepted" : "line search failed");
+    if (!accepted) {
+      if (rep) rep->rs_iters += it;
+      return fail(PF_ENOTCONV, "damage solve: line search failed at ||Phi|| %.3e", phi);
+    }
   }
   if (rep) rep->rs_iters += it;
   return PF_OK;
@@ -845,8 +869,17 @@ pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step
   const double omega = o.algo == PF_ALGO_AM ? 1.0 : o.omega;
   pf_status last = PF_ENOTCONV;
   for (int k = 1; k <= o.am_maxit; ++k) {
-    pf_status st1 = u_solve(s, st, o, rep);
-    if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
+    // u-subproblem (Algorithm 2, first line of the loop).  If neither alpha nor the load has
+    // changed since the last solve, K(alpha) and the right-hand side are bitwise the same and
+    // so is the minimizer u~: it is reused.
+    if (!(s.xu_valid && s.xu_precision == o.precision)) {
+      pf_status st1 = u_solve(s, st, o, rep);
+      if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
+      s.xu_valid = st1 == PF_OK;
+      s.xu_precision = o.precision;
+    } else if (rep) {
+      rep->u_solves_reused++;
+    }
     relax_u(st, s.u, s.xu, omega, n2, slot(s, S_DU));
     double du[2];
     TRY(read_scalars(s, st, S_DU, 2, du));
@@ -859,7 +892,7 @@ pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step
     relax_alpha(st, g, s.alpha, s.xrs, s.alpha_prev, wbar, s.alpha32, slot(s, S_DALPHA));
     double da;
     TRY(read_scalars(s, st, S_DALPHA, 1, &da));
-    if (da > 0.0) s.elastic_ready64 = s.elastic_ready32 = false;
+    if (da > 0.0) s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
     double durel = du[1] > 0.0 ? du[0] / du[1] : du[0];
     if (rep) {
       rep->am_iters = k;
@@ -1064,7 +1097,7 @@ pf_status pf_set_material(pf_sim* s, const pf_material* mi) {
   s->m = m;
   s->mat_in = *mi;
   s->have_material = true;
-  s->elastic_ready64 = s->elastic_ready32 = false;
+  s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   return PF_OK;
 }
 
@@ -1146,7 +1179,7 @@ pf_status pf_set_fields(pf_sim* s, const double* u, const double* alpha, const d
   }
   if (alpha_prev) CU(cudaMemcpy(s->alpha_prev, alpha_prev, n * sizeof(double), cudaMemcpyHostToDevice));
   CU(cudaDeviceSynchronize());
-  s->elastic_ready64 = s->elastic_ready32 = false;
+  s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   return PF_OK;
 }
 
@@ -1254,7 +1287,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
   CU(cudaSetDevice(s->ctx->device));
   s->r_scale = 0.0;
   s->use_graphs = o->use_graphs != 0;
-  s->elastic_ready64 = s->elastic_ready32 = false;
+  s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   pf_step_report r{};
   pf_status status = u_solve(*s, st, *o, &r);
   if (status == PF_OK || status == PF_ENOTCONV)
@@ -1279,7 +1312,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
     const size_t n = s->lv[0].g.n;
     CU(cudaMemcpyAsync(s->alpha, s->xrs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     vec_convert<float, double>(st, s->alpha32, s->alpha, n);
-    s->elastic_ready64 = s->elastic_ready32 = false;
+    s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   }
   CU(cudaStreamSynchronize(st));
   if (rep) *rep = r;

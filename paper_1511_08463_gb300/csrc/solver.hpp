@@ -90,6 +90,9 @@ struct pf_sim {
   // MG state validity
   bool elastic_ready64 = false, elastic_ready32 = false, damage_ready64 = false,
        damage_ready32 = false;
+  // xu holds the u-subproblem minimizer for the current alpha and load
+  bool xu_valid = false;
+  int xu_precision = -1;
   size_t ws_used = 0;
   bool busy = false;
   // CUDA graphs holding one whole PCG solve each (device-side while loop), per operator

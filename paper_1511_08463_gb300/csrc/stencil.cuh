@@ -395,11 +395,14 @@ struct DamageOp {
       double xv = double(own.p), F = double(f);
       double l = args.lo[node], h = upper(X2, Y2, l);
       double ph = mcp_phi(xv, F, l, h);
-      bool active = (h - l <= args.zeta) || (xv <= l + args.zeta && F > 0.0) || (xv >= h - args.zeta && F < 0.0);
+      // eq. reducedis with both bounds; a single-point box counts as lower-active
+      const bool lower = (h - l <= args.zeta) || (xv <= l + args.zeta && F > 0.0);
+      const bool upper = !lower && (xv >= h - args.zeta && F < 0.0);
+      const bool active = lower || upper;
       args.y[node] = T(F);
       args.dout[node] = T(ph);
       args.rhs[node] = active ? T(0) : T(-F);
-      args.act[node] = active ? 1 : 0;
+      args.act[node] = lower ? 1 : (upper ? 2 : 0);
       if (MODE == M_TRIAL) args.xt[node] = own.p;
       red[0] += T(ph * ph);
       red[1] += active ? T(0) : T(F * F);

@@ -124,11 +124,13 @@ def bar(nx: int = 128, ny: int = 16, n_steps: int = 20, ell: float = 0.05, model
         pins=[(0, ny, "uy", 0.0)], alpha_boxes=boxes, loads=loads, omega=1.0)
 
 
-def notched_square(n: int = 512, n_steps: int = 50, t_max: float = 0.6, ell_over_h: float = 4.0,
+def notched_square(n: int = 512, n_steps: int = 50, t_max: float = 2.0, ell_over_h: float = 4.0,
                    model: str = "AT1", nu: float = 0.3, omega: float = 1.5,
                    k_ell: float = 1e-6) -> Workload:
     """Single-edge notched unit square in Mode I on an n x n crossed mesh: notch x <= 0.5,
-    |y - 0.5| <= h (two elements wide); bottom clamped; top u_x = 0, u_y = t; sides free."""
+    |y - 0.5| <= h (two elements wide); bottom clamped; top u_x = 0, u_y = t; sides free;
+    t_k = k t_max / n_steps.  With t_max = 2 the crack starts near t = 1.2-1.3 (AT1, ell = 4h,
+    E = Gc = 1) and crosses the ligament before the last step."""
     if n % 2:
         raise ValueError("n must be even")
     h = 1.0 / n
@@ -164,7 +166,7 @@ def ly_default(nx: int, ny: int) -> float:
 
 
 def batch_of_notched(n_instances: int = 256, lo: int = 64, hi: int = 256, seed: int = 0,
-                     multiple: int = 16, n_steps: int = 50, t_max: float = 0.6) -> List[Workload]:
+                     multiple: int = 16, n_steps: int = 50, t_max: float = 2.0) -> List[Workload]:
     """Batched notched squares: N log-uniform on [lo, hi] rounded to a multiple of 16, ell
     uniform in [2h, 8h], nu uniform in [0.2, 0.35]; one step each to t ~ U[0.5, 1.0]*t_max."""
     rng = np.random.default_rng(seed)
