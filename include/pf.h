@@ -230,6 +230,14 @@ pf_status pf_op_damage_gradient(pf_sim* sim, double* F, double* Phi, uint8_t* ac
  * values). */
 pf_status pf_op_damage_apply(pf_sim* sim, int precision, const void* x, void* y, void* stream);
 
+/* Off-diagonal block of the Newton Jacobian of the coupled system (Section 3.3, eq. offdiag),
+ * B = E_u,alpha at the resident u, alpha and current load, in FP64: transpose == 0 gives
+ * y = B x (x: n_nodes damage values, y: 2*n_nodes interleaved displacement values, 0 on
+ * prescribed dofs); transpose == 1 gives y = B^T x (x: 2*n_nodes, prescribed dofs ignored; y:
+ * n_nodes).  Device pointers, caller-owned.  Synchronous. */
+pf_status pf_op_coupling_apply(pf_sim* sim, int transpose, const double* x, double* y,
+                               void* stream);
+
 /* Solve the u-subproblem of Algorithm 1 at the resident alpha and current load, in place
  * (u <- minimizer; Section 3.1 solver: PCG + multigrid).  rep may be NULL. */
 pf_status pf_op_u_solve(pf_sim* sim, const pf_solver_opts* o, void* stream, pf_step_report* rep);

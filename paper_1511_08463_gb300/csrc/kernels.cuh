@@ -108,4 +108,14 @@ void snap_active(cudaStream_t s, const Grid& g, const uint8_t* act, const double
 // d = -(dg + Hv)
 void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d);
 
+// ---- Newton (ORAM-N) helpers (ops_newton.cu) ---------------------------------------------------
+template <class T>
+void launch_coupling(cudaStream_t s, const Grid& g, const Mat& m, bool transpose,
+                     const CouplingArgs<T>& a);
+template <class T>
+void vec_lincomb(cudaStream_t s, T* z, T a, const T* x, T b, const T* y, T c, size_t n);
+void newton_trial(cudaStream_t s, const Grid& g, double* u, const double* u0, const double* du,
+                  double* alpha, const double* a0, const double* da, const double* lo, float* a32,
+                  double mu);
+
 }  // namespace pf

@@ -219,6 +219,13 @@ void layout(pf_sim& s, Arena& a) {
   s.act = a.take<uint8_t>(n);
   s.acttr = a.take<uint8_t>(n);
   s.tmp32 = a.take<float>(n2);
+  s.u32 = a.take<float>(n2);
+  s.eig32 = a.take<float>((size_t)g.ny * elems_per_cell(g.kind));
+  for (int k = 0; k < 12; ++k) s.nv[k] = a.take<float>(3 * n);
+  s.nu0 = a.take<double>(n2);
+  s.na0 = a.take<double>(n);
+  s.ndu = a.take<double>(n2);
+  s.nda = a.take<double>(n);
   take_krylov(a, s.k64, n2);
   take_krylov(a, s.k32, n2);
   for (int l = 0; l < L; ++l) {
@@ -627,6 +634,7 @@ pf_status set_load(pf_sim& s, double t, double dT, cudaStream_t st) {
         tab[(size_t)j * NE + t2] = s.mat_in.beta * (-dT * erfc(y / s.mat_in.pen));
       }
     CU(cudaMemcpyAsync(s.eig, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    vec_convert<float, double>(st, s.eig32, s.eig, tab.size());
     CU(cudaStreamSynchronize(st));
   }
   CU(cudaGetLastError());
@@ -863,49 +871,281 @@ pf_status begin_step(pf_sim& s, cudaStream_t st, const pf_load& L) {
   return PF_OK;
 }
 
-pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
+// One pass of the loop of Algorithm 2 (Algorithm 1 when omega = 1): returns the damage change
+// max|alpha^k - alpha^{k-1}| and the relative displacement change.
+pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep,
+                         double omega, double* da_out, double* durel_out) {
   const Grid& g = s.lv[0].g;
   const size_t n2 = 2 * (size_t)g.n;
+  // u-subproblem (Algorithm 2, first line of the loop).  If neither alpha nor the load has
+  // changed since the last solve, K(alpha) and the right-hand side are bitwise the same and
+  // so is the minimizer u~: it is reused.
+  if (!(s.xu_valid && s.xu_precision == o.precision)) {
+    pf_status st1 = u_solve(s, st, o, rep);
+    if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
+    s.xu_valid = st1 == PF_OK;
+    s.xu_precision = o.precision;
+  } else if (rep) {
+    rep->u_solves_reused++;
+  }
+  relax_u(st, s.u, s.xu, omega, n2, slot(s, S_DU));
+  double du[2];
+  TRY(read_scalars(s, st, S_DU, 2, du));
+  pf_status st2 = alpha_solve(s, st, o, rep);
+  if (st2 != PF_OK && st2 != PF_ENOTCONV) return st2;
+  omega_star(st, g, s.alpha, s.xrs, s.alpha_prev, slot(s, S_OMEGA));
+  double ms;
+  TRY(read_scalars(s, st, S_OMEGA, 1, &ms));
+  double wbar = choose_omega_bar(omega, -ms);
+  relax_alpha(st, g, s.alpha, s.xrs, s.alpha_prev, wbar, s.alpha32, slot(s, S_DALPHA));
+  double da;
+  TRY(read_scalars(s, st, S_DALPHA, 1, &da));
+  if (da > 0.0) s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
+  *da_out = da;
+  *durel_out = du[1] > 0.0 ? du[0] / du[1] : du[0];
+  if (rep) rep->omega_bar_min = std::min(rep->omega_bar_min, wbar);
+  return PF_OK;
+}
+
+pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
   const double omega = o.algo == PF_ALGO_AM ? 1.0 : o.omega;
-  pf_status last = PF_ENOTCONV;
   for (int k = 1; k <= o.am_maxit; ++k) {
-    // u-subproblem (Algorithm 2, first line of the loop).  If neither alpha nor the load has
-    // changed since the last solve, K(alpha) and the right-hand side are bitwise the same and
-    // so is the minimizer u~: it is reused.
-    if (!(s.xu_valid && s.xu_precision == o.precision)) {
-      pf_status st1 = u_solve(s, st, o, rep);
-      if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
-      s.xu_valid = st1 == PF_OK;
-      s.xu_precision = o.precision;
-    } else if (rep) {
-      rep->u_solves_reused++;
-    }
-    relax_u(st, s.u, s.xu, omega, n2, slot(s, S_DU));
-    double du[2];
-    TRY(read_scalars(s, st, S_DU, 2, du));
-    pf_status st2 = alpha_solve(s, st, o, rep);
-    if (st2 != PF_OK && st2 != PF_ENOTCONV) return st2;
-    omega_star(st, g, s.alpha, s.xrs, s.alpha_prev, slot(s, S_OMEGA));
-    double ms;
-    TRY(read_scalars(s, st, S_OMEGA, 1, &ms));
-    double wbar = choose_omega_bar(omega, -ms);
-    relax_alpha(st, g, s.alpha, s.xrs, s.alpha_prev, wbar, s.alpha32, slot(s, S_DALPHA));
-    double da;
-    TRY(read_scalars(s, st, S_DALPHA, 1, &da));
-    if (da > 0.0) s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
-    double durel = du[1] > 0.0 ? du[0] / du[1] : du[0];
+    double da, durel;
+    TRY(oram_iteration(s, st, o, rep, omega, &da, &durel));
     if (rep) {
       rep->am_iters = k;
       rep->dalpha_inf = da;
       rep->du_rel = durel;
-      rep->omega_bar_min = std::min(rep->omega_bar_min, wbar);
     }
-    if (da <= o.am_tol && durel <= o.am_tol) {
-      last = PF_OK;
-      break;
+    if (da <= o.am_tol && durel <= o.am_tol) return PF_OK;
+  }
+  return PF_ENOTCONV;
+}
+
+// ---------------------------------------------------------------------------------------------
+// ORAM-N (Algorithm 3): ORAM until the optimality residual has dropped by switch_tol, then the
+// reduced-space active-set Newton method (Algorithm 4) on the coupled system (u, alpha), whose
+// reduced Jacobian J_NN = [[A, B], [B^T, C]] (Section 3.3, eq. inactjac) is solved by MINRES
+// with the block preconditioner of eq. preconditioner (S ~ C), each inverse action approximated
+// by two multigrid V-cycles.  The Krylov solve runs in FP32; residuals, line search and active
+// set in FP64.
+// ---------------------------------------------------------------------------------------------
+inline float* upart(float* x) { return x; }
+inline float* apart(pf_sim& s, float* x) { return x + 2 * (size_t)s.lv[0].g.n; }
+
+// y = J_NN x: y_u = K x_u + B x_a, y_a = B^T x_u + H_NN x_a (masks: fixed u dofs, active alpha)
+void jac_apply(pf_sim& s, cudaStream_t st, float* x, float* y) {
+  const Grid& g = s.lv[0].g;
+  apply_op<float>(s, st, ELASTIC, 0, upart(x), upart(y), false, S_TMP);
+  apply_op<float>(s, st, DAMAGE, 0, apart(s, x), apart(s, y), false, S_TMP);
+  CouplingArgs<float> b{};
+  b.u = s.u32;
+  b.alpha = s.alpha32;
+  b.eig = s.thermal ? s.eig32 : nullptr;
+  b.excl = s.act;
+  b.accumulate = 1;
+  b.x = apart(s, x);
+  b.y = upart(y);
+  launch_coupling<float>(st, g, s.m, false, b);
+  b.x = upart(x);
+  b.y = apart(s, y);
+  launch_coupling<float>(st, g, s.m, true, b);
+}
+
+// two V-cycles of the operator's multigrid: x = V r; x += V (r - A x)
+void two_vcycles(pf_sim& s, cudaStream_t st, int phys, float* r, float* x, float* t, float* e,
+                 int deg) {
+  const size_t nd = (size_t)(phys == ELASTIC ? 2 : 1) * s.lv[0].g.n;
+  precond<float>(s, st, phys, r, x, deg);
+  residual_op<float>(s, st, phys, 0, r, x, t);
+  precond<float>(s, st, phys, t, e, deg);
+  vec_add<float>(st, x, e, nd);
+}
+
+// z = P^{-1} r, eq. preconditioner: y1 = A^-1 r_u; z_a = C^-1 (r_a - B^T y1); z_u = A^-1 (r_u - B z_a)
+void block_prec(pf_sim& s, cudaStream_t st, float* r, float* z, int deg) {
+  const Grid& g = s.lv[0].g;
+  const size_t n = g.n;
+  float *y1 = s.nv[8], *t = s.nv[9], *e = s.nv[10], *w = s.nv[11];
+  two_vcycles(s, st, ELASTIC, upart(r), upart(y1), upart(t), upart(e), deg);
+  CouplingArgs<float> b{};
+  b.u = s.u32;
+  b.alpha = s.alpha32;
+  b.eig = s.thermal ? s.eig32 : nullptr;
+  b.excl = s.act;
+  b.accumulate = 0;
+  b.x = upart(y1);
+  b.y = apart(s, w);
+  launch_coupling<float>(st, g, s.m, true, b);                            // w_a = B^T y1
+  vec_lincomb<float>(st, apart(s, w), 1.f, apart(s, r), -1.f, apart(s, w), 0.f, n);  // r_a - w_a
+  two_vcycles(s, st, DAMAGE, apart(s, w), apart(s, z), apart(s, t), apart(s, e), deg);
+  b.x = apart(s, z);
+  b.y = upart(w);
+  launch_coupling<float>(st, g, s.m, false, b);                           // w_u = B z_a
+  vec_lincomb<float>(st, upart(w), 1.f, upart(r), -1.f, upart(w), 0.f, 2 * n);  // r_u - w_u
+  two_vcycles(s, st, ELASTIC, upart(w), upart(z), upart(t), upart(e), deg);
+}
+
+pf_status dot3(pf_sim& s, cudaStream_t st, const float* x, const float* y, double* out) {
+  vec_dot<float>(st, x, y, 3 * (size_t)s.lv[0].g.n, slot(s, S_TMP));
+  return read_scalars(s, st, S_TMP, 1, out);
+}
+
+// Preconditioned MINRES (Paige & Saunders) for J_NN x = b from x = 0 (x may be b's storage);
+// stops when the preconditioned residual estimate drops below rtol times its initial value.
+pf_status minres(pf_sim& s, cudaStream_t st, float* b, float* x, double rtol, int maxit, int deg,
+                 int64_t* its) {
+  const size_t N = 3 * (size_t)s.lv[0].g.n;
+  float *r1 = s.nv[0], *r2 = s.nv[1], *y = s.nv[2], *v = s.nv[3], *w = s.nv[4], *w1 = s.nv[5],
+        *w2 = s.nv[6];
+  CU(cudaMemcpyAsync(r1, b, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  vec_fill<float>(st, x, 0.f, N);  // after the copy: x may share storage with b
+  vec_fill<float>(st, w, 0.f, N);
+  vec_fill<float>(st, w2, 0.f, N);
+  block_prec(s, st, r1, y, deg);
+  double beta1;
+  TRY(dot3(s, st, r1, y, &beta1));
+  if (!(beta1 >= 0.0)) return fail(PF_ENUMERIC, "MINRES: preconditioner not positive definite");
+  beta1 = sqrt(beta1);
+  if (beta1 == 0.0) return PF_OK;
+  CU(cudaMemcpyAsync(r2, r1, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  double oldb = 0.0, beta = beta1, dbar = 0.0, epsln = 0.0, phibar = beta1, cs = -1.0, sn = 0.0;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    const double sc = 1.0 / beta;
+    vec_lincomb<float>(st, v, float(sc), y, 0.f, nullptr, 0.f, N);  // v = y / beta
+    jac_apply(s, st, v, y);                                        // y = J v
+    if (it >= 2) vec_lincomb<float>(st, y, 1.f, y, float(-beta / oldb), r1, 0.f, N);
+    double alfa;
+    TRY(dot3(s, st, v, y, &alfa));
+    vec_lincomb<float>(st, y, 1.f, y, float(-alfa / beta), r2, 0.f, N);
+    std::swap(r1, r2);  // r1 <- r2, r2 <- y (copied below)
+    CU(cudaMemcpyAsync(r2, y, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    block_prec(s, st, r2, y, deg);
+    oldb = beta;
+    double bb;
+    TRY(dot3(s, st, r2, y, &bb));
+    if (!(bb >= 0.0)) return fail(PF_ENUMERIC, "MINRES: preconditioner not positive definite");
+    beta = sqrt(bb);
+    const double oldeps = epsln;
+    const double delta = cs * dbar + sn * alfa;
+    const double gbar = sn * dbar - cs * alfa;
+    epsln = sn * beta;
+    dbar = -cs * beta;
+    const double gamma = std::max(hypot(gbar, beta), 1e-300);
+    cs = gbar / gamma;
+    sn = beta / gamma;
+    const double phi = cs * phibar;
+    phibar = sn * phibar;
+    // w = (v - oldeps w1 - delta w2) / gamma with (w1, w2) <- (w2, w)
+    std::swap(w1, w2);
+    std::swap(w2, w);
+    vec_lincomb<float>(st, w, float(1.0 / gamma), v, float(-oldeps / gamma), w1, 0.f, N);
+    vec_lincomb<float>(st, w, 1.f, w, float(-delta / gamma), w2, 0.f, N);
+    vec_lincomb<float>(st, x, float(phi), w, 0.f, nullptr, 1.f, N);
+    if (phibar <= rtol * beta1 || beta == 0.0) break;
+  }
+  if (its) *its += std::min(it, maxit);
+  return PF_OK;
+}
+
+// ||Phi|| of the coupled optimality system at the resident state; leaves F, Phi, act, rhs of
+// the damage part in the sim's main buffers and r64 = -E_u.
+pf_status coupled_residual(pf_sim& s, cudaStream_t st, double zeta, double* nrm) {
+  double rn;
+  TRY(physical_residual(s, st, s.u, s.r64, &rn));
+  damage_q(st, s.lv[0].g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, s.lv[0].f64.wD,
+           s.lv[0].f32.wD);
+  double v[2];
+  TRY(grad_at(s, st, s.alpha, zeta, s.F, s.Phi, s.rhs, s.act, v));
+  *nrm = sqrt(rn * rn + v[0]);
+  return PF_OK;
+}
+
+// Algorithm 4 on the coupled system: reduced Newton steps with a projected line search on
+// ||Phi||^2.  Returns PF_OK when ||Phi|| <= tol, PF_ENOTCONV otherwise (state = best point).
+pf_status newton_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep,
+                       double tol, double* phi_out) {
+  const Grid& g = s.lv[0].g;
+  const size_t n = g.n, n2 = 2 * n;
+  double phi;
+  TRY(coupled_residual(s, st, o.zeta, &phi));
+  for (int it = 0; it < o.newton_maxit; ++it) {
+    *phi_out = phi;
+    if (phi <= tol) return PF_OK;
+    if (rep) rep->newton_iters++;
+    // operators at the current state (FP32 inner solves)
+    vec_convert<float, double>(st, s.u32, s.u, n2);
+    setup_elastic<float>(s, st);
+    setup_damage<float>(s, st);
+    damage_masks<float>(s, st);
+    // right-hand side -F_N = [r64 ; rhs]; the solution overwrites it
+    float* xs = s.nv[7];
+    vec_convert<float, double>(st, xs, s.r64, n2);
+    vec_convert<float, double>(st, xs + n2, s.rhs, n);
+    int64_t kits = 0;
+    TRY(minres(s, st, xs, xs, o.minres_rtol, o.minres_maxit, o.mg_degree, &kits));
+    if (rep) rep->krylov_iters_newton += kits;
+    vec_convert<double, float>(st, s.ndu, xs, n2);
+    vec_convert<double, float>(st, s.nda, xs + n2, n);
+    snap_active(st, g, s.act, s.alpha, s.alpha_prev, s.nda);
+    // projected line search (alpha clipped to its box; u unbounded)
+    CU(cudaMemcpyAsync(s.nu0, s.u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(s.na0, s.alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    bool accepted = false;
+    const double phi2 = phi * phi;
+    for (double mu = 1.0; mu >= 0x1p-20; mu *= 0.5) {
+      newton_trial(st, g, s.u, s.nu0, s.ndu, s.alpha, s.na0, s.nda, s.alpha_prev, s.alpha32, mu);
+      double pt;
+      TRY(coupled_residual(s, st, o.zeta, &pt));
+      if (pt * pt <= (1.0 - 2.0 * 1e-4 * mu) * phi2) {
+        phi = pt;
+        accepted = true;
+        break;
+      }
+    }
+    s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
+    if (!accepted) {  // restore the step's starting point
+      CU(cudaMemcpyAsync(s.u, s.nu0, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(s.alpha, s.na0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      vec_convert<float, double>(st, s.alpha32, s.alpha, n);
+      TRY(coupled_residual(s, st, o.zeta, &phi));
+      *phi_out = phi;
+      return PF_ENOTCONV;
     }
   }
-  return last;
+  *phi_out = phi;
+  return phi <= tol ? PF_OK : PF_ENOTCONV;
+}
+
+pf_status oramn_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
+  double phi_start;
+  TRY(coupled_residual(s, st, o.zeta, &phi_start));
+  const double tol = o.newton_rtol * phi_start;
+  if (rep) rep->phi_start = phi_start;
+  int oram_its = 0;
+  const int max_outer = 50;
+  double phi = phi_start;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    double phi0;
+    TRY(coupled_residual(s, st, o.zeta, &phi0));
+    phi = phi0;
+    if (phi0 <= tol) break;
+    while (phi / phi0 > o.switch_tol && phi > tol && oram_its < o.am_maxit) {
+      double da, durel;
+      TRY(oram_iteration(s, st, o, rep, o.omega, &da, &durel));
+      ++oram_its;
+      if (rep) rep->am_iters = oram_its;
+      TRY(coupled_residual(s, st, o.zeta, &phi));
+    }
+    if (phi <= tol) break;
+    pf_status ns = newton_solve(s, st, o, rep, tol, &phi);
+    if (ns == PF_OK) break;
+    if (ns != PF_ENOTCONV) return ns;
+    if (oram_its >= o.am_maxit) break;
+  }
+  if (rep) rep->phi_norm = phi;
+  return phi <= tol ? PF_OK : PF_ENOTCONV;
 }
 
 }  // namespace
@@ -1110,6 +1350,11 @@ static pf_status check_opts(const pf_solver_opts* o) {
   if (!(o->omega > 0.0 && o->omega < 2.0)) return fail(PF_EINVAL, "omega must lie in (0, 2)");
   if (o->am_maxit < 1 || o->cg_maxit < 1 || o->rs_maxit < 1 || o->mg_degree < 1)
     return fail(PF_EINVAL, "iteration limits must be positive");
+  if (o->algo == PF_ALGO_ORAM_N &&
+      (o->newton_maxit < 1 || o->minres_maxit < 1 || !(o->switch_tol > 0.0 && o->switch_tol < 1.0) ||
+       !(o->newton_rtol > 0.0) || !(o->minres_rtol > 0.0 && o->minres_rtol < 1.0)))
+    return fail(PF_EINVAL, "ORAM-N needs newton_maxit, minres_maxit >= 1, switch_tol and "
+                           "minres_rtol in (0, 1), newton_rtol > 0");
   return PF_OK;
 }
 
@@ -1127,7 +1372,8 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   pf_step_report r{};
   r.omega_bar_min = o->omega;
   pf_status status = begin_step(*s, st, *L);
-  if (status == PF_OK) status = oram_step(*s, st, *o, &r);
+  if (status == PF_OK)
+    status = o->algo == PF_ALGO_ORAM_N ? oramn_step(*s, st, *o, &r) : oram_step(*s, st, *o, &r);
   if (status == PF_OK || status == PF_ENOTCONV) {
     pf_status e2 = energy_now(*s, st, r.energy);
     if (e2 != PF_OK) status = e2;
@@ -1274,6 +1520,25 @@ pf_status pf_op_damage_apply(pf_sim* s, int precision, const void* x, void* y, v
   } else {
     return fail(PF_EINVAL, "unknown precision");
   }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+pf_status pf_op_coupling_apply(pf_sim* s, int transpose, const double* x, double* y,
+                               void* stream) {
+  if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  if (transpose != 0 && transpose != 1) return fail(PF_EINVAL, "transpose must be 0 or 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CU(cudaSetDevice(s->ctx->device));
+  CouplingArgs<double> b{};
+  b.u = s->u;
+  b.alpha = s->alpha;
+  b.eig = s->thermal ? s->eig : nullptr;
+  b.x = x;
+  b.y = y;
+  launch_coupling<double>(st, s->lv[0].g, s->m, transpose == 1, b);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   return PF_OK;

@@ -79,6 +79,11 @@ struct pf_sim {
   double *tmpa = nullptr, *tmpb = nullptr;
   uint8_t *act = nullptr, *acttr = nullptr;
   float* tmp32 = nullptr;
+  // Newton (ORAM-N): FP32 copies of the state, 12 work vectors of 3n floats ([u | alpha]),
+  // FP64 step start and direction
+  float *u32 = nullptr, *eig32 = nullptr;
+  float* nv[12] = {};
+  double *nu0 = nullptr, *na0 = nullptr, *ndu = nullptr, *nda = nullptr;
   pf::Krylov<double> k64;
   pf::Krylov<float> k32;
   // reductions

@@ -410,4 +410,152 @@ struct DamageOp {
   }
 };
 
+// ----------------------------------------------------------------------------------------------
+// coupling block E_ua of the Newton Jacobian (Section 1.2 eq. offdiag, Section 3.3 block B):
+//   B_ij = int a'(alpha_h) A0 eps_eff(u) : eps(phi_i) phi_j,  a'(alpha) = -2 (1 - alpha),
+// per element  int_T a'(alpha_h) phi_j = -2 |T| (1/3 - (alpha_j + S_alpha) / 12)  (P1 mass matrix).
+//   CouplingOp<T, K, false>: y_u (+)= B x_alpha  (x_alpha read as 0 on excluded alpha nodes;
+//                            y_u zero on prescribed displacement dofs)
+//   CouplingOp<T, K, true>:  y_a (+)= B^T x_u    (x_u read as 0 on prescribed dofs; y_a zero on
+//                            excluded alpha nodes)
+// ----------------------------------------------------------------------------------------------
+template <class T>
+struct CouplingArgs {
+  const T* x;         // input: x_alpha (n) or x_u (2n)
+  const T* u;         // state displacement (2n)
+  const T* alpha;     // state damage (n)
+  const T* eig;       // eps0 per (cell row, element) or null
+  const uint8_t* excl;  // alpha exclusion mask (active set), may be null
+  T* y;               // output (2n for B, n for B^T)
+  int accumulate;     // 1: y += result
+  RedSlot slot;
+  int coarse;
+};
+
+template <class T, int KIND_, bool TRANSPOSE>
+struct CouplingOp {
+  static constexpr int KIND = KIND_;
+  static constexpr int NR = 0;
+  static constexpr bool RED_MAX = false;
+  using RT = T;
+  using ET = T;
+  static constexpr int NRC = TRANSPOSE ? 2 : 3;
+  struct V {
+    T x0, x1, ux, uy, a;  // input (x0 = x_alpha or x_u,x; x1 = x_u,y), state u, alpha
+  };
+  struct R {
+    T c[NRC];
+  };
+  struct Acc {
+    T c[4];
+  };
+  Grid g;
+  Mat m;
+  Consts<T> cs;
+  CouplingArgs<T> args;
+
+  __device__ static V zero() { return V{T(0), T(0), T(0), T(0), T(0)}; }
+  __device__ static Acc acc0() { return Acc{{T(0), T(0), T(0), T(0)}}; }
+
+  __device__ V load(int node, int X2, int Y2) const {
+    V v;
+    if (TRANSPOSE) {
+      v.x0 = is_fixed(g, X2, Y2, 0) ? T(0) : args.x[2 * node];
+      v.x1 = is_fixed(g, X2, Y2, 1) ? T(0) : args.x[2 * node + 1];
+    } else {
+      v.x0 = (args.excl && args.excl[node]) ? T(0) : args.x[node];
+      v.x1 = T(0);
+    }
+    v.ux = args.u[2 * node];
+    v.uy = args.u[2 * node + 1];
+    v.a = args.alpha[node];
+    return v;
+  }
+
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
+    R r;
+    if (!valid) {
+#pragma unroll
+      for (int c = 0; c < NRC; ++c) r.c[c] = T(0);
+      return r;
+    }
+    constexpr int NE = elems_per_cell(KIND);
+    const T ihx = cs.ihx, ihy = cs.ihy;
+    // stress of the state: sigma = A0 (eps(u) - eps0)
+    T exx = ihx * (T(gx(KIND, t, 0)) * n0.ux + T(gx(KIND, t, 1)) * n1.ux + T(gx(KIND, t, 2)) * n2.ux);
+    T eyy = ihy * (T(gy(KIND, t, 0)) * n0.uy + T(gy(KIND, t, 1)) * n1.uy + T(gy(KIND, t, 2)) * n2.uy);
+    T gxy = ihy * (T(gy(KIND, t, 0)) * n0.ux + T(gy(KIND, t, 1)) * n1.ux + T(gy(KIND, t, 2)) * n2.ux) +
+            ihx * (T(gx(KIND, t, 0)) * n0.uy + T(gx(KIND, t, 1)) * n1.uy + T(gx(KIND, t, 2)) * n2.uy);
+    if (args.eig) {
+      T e0 = args.eig[cj * NE + t];
+      exx -= e0;
+      eyy -= e0;
+    }
+    const T sxx = cs.lam2mu * exx + cs.lam * eyy, syy = cs.lam * exx + cs.lam2mu * eyy,
+            sxy = cs.mu * gxy;
+    const T Sa = n0.a + n1.a + n2.a;
+    const T area = cs.area;
+    if (!TRANSPOSE) {
+      // s_T = sum_j int_T a'(alpha_h) phi_j x_alpha,j
+      const T w0 = T(-2) * area * (T(1.0 / 3.0) - (n0.a + Sa) * T(1.0 / 12.0));
+      const T w1 = T(-2) * area * (T(1.0 / 3.0) - (n1.a + Sa) * T(1.0 / 12.0));
+      const T w2 = T(-2) * area * (T(1.0 / 3.0) - (n2.a + Sa) * T(1.0 / 12.0));
+      const T sT = w0 * n0.x0 + w1 * n1.x0 + w2 * n2.x0;
+      r.c[0] = sT * sxx;
+      r.c[1] = sT * syy;
+      r.c[2] = sT * sxy;
+    } else {
+      // e_T = sigma : eps(x_u); node j receives -2|T| (1/3 - (alpha_j + S_a)/12) e_T
+      T dxx = ihx * (T(gx(KIND, t, 0)) * n0.x0 + T(gx(KIND, t, 1)) * n1.x0 + T(gx(KIND, t, 2)) * n2.x0);
+      T dyy = ihy * (T(gy(KIND, t, 0)) * n0.x1 + T(gy(KIND, t, 1)) * n1.x1 + T(gy(KIND, t, 2)) * n2.x1);
+      T dxy = ihy * (T(gy(KIND, t, 0)) * n0.x0 + T(gy(KIND, t, 1)) * n1.x0 + T(gy(KIND, t, 2)) * n2.x0) +
+              ihx * (T(gx(KIND, t, 0)) * n0.x1 + T(gx(KIND, t, 1)) * n1.x1 + T(gx(KIND, t, 2)) * n2.x1);
+      const T eT = sxx * dxx + syy * dyy + sxy * dxy;
+      r.c[0] = T(-2) * area * eT * (T(1.0 / 3.0) - Sa * T(1.0 / 12.0));  // node-independent part
+      r.c[1] = T(2) * area * eT * T(1.0 / 12.0);                         // times alpha_j
+    }
+    return r;
+  }
+
+  template <int t, int k>
+  __device__ void add(Acc& a, const R& r) const {
+    if (!TRANSPOSE) {
+      constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
+      if (cx != 0) {
+        a.c[0] += T(cx) * r.c[0];
+        a.c[2] += T(cx) * r.c[2];
+      }
+      if (cy != 0) {
+        a.c[1] += T(cy) * r.c[2];
+        a.c[3] += T(cy) * r.c[1];
+      }
+    } else {
+      a.c[0] += r.c[0];
+      a.c[1] += r.c[1];
+    }
+  }
+
+  __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
+                        RT (&red)[1]) const {
+    if (!TRANSPOSE) {
+      T fx = cs.ihx * a.c[0] + cs.ihy * a.c[1];
+      T fy = cs.ihx * a.c[2] + cs.ihy * a.c[3];
+      if (is_fixed(g, X2, Y2, 0)) fx = T(0);
+      if (is_fixed(g, X2, Y2, 1)) fy = T(0);
+      if (args.accumulate) {
+        fx += args.y[2 * node];
+        fy += args.y[2 * node + 1];
+      }
+      args.y[2 * node] = fx;
+      args.y[2 * node + 1] = fy;
+    } else {
+      T f = a.c[0] + a.c[1] * own.a;
+      if (args.excl && args.excl[node]) f = T(0);
+      if (args.accumulate) f += args.y[node];
+      args.y[node] = f;
+    }
+  }
+};
+
 }  // namespace pf

@@ -195,6 +195,15 @@ class Sim:
                                             C.c_void_p(_stream(stream))))
         return y
 
+    def coupling_apply(self, x: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
+        """y = B x (x: n damage values -> 2n displacement values) or B^T x (2n -> n), FP64."""
+        x = x.to(torch.float64).contiguous()
+        n = self.n_nodes
+        y = torch.empty(n if transpose else 2 * n, dtype=torch.float64, device=x.device)
+        B.check(self.lib.pf_op_coupling_apply(self.h, 1 if transpose else 0, _ptr(x), _ptr(y),
+                                              C.c_void_p(_stream(stream))))
+        return y
+
     def u_solve(self, opts=None, stream=None):
         o = opts or make_opts()
         rep = B.pf_step_report()
