@@ -45,6 +45,13 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven CG loops (per-kernel profilers cannot see inside graphs)")
     ap.add_argument("--quiet", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=32,
+                    help="jobs in the serving sample (0: no serving leg)")
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-max-n", type=int, default=256, help="largest serving mesh N")
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-arena-gb", type=float, default=16.0)
+    ap.add_argument("--serve-only", action="store_true", help="run the serving leg alone")
     return ap.parse_args()
 
 
@@ -243,6 +250,45 @@ def traffic_from_profiles(kclass: str):
     return None
 
 
+def serve_record(args, ctx):
+    """Serving leg: a seeded Poisson stream of notched-square and bar jobs (N log-uniform on
+    [32, serve_max_n], 10-60 load steps each, mixed precision) through the libpf request loop;
+    per-load-step latency = end of the step minus the moment it became ready (arrival for the
+    first step), so admission and worker queueing are included."""
+    import numpy as np
+
+    import workloads as W
+    from paper_1511_08463_gb300 import sim as S
+
+    jobs = W.serving_stream(n_jobs=args.serve_jobs, rate=args.serve_rate, seed=0, lo=32,
+                            hi=args.serve_max_n)
+    arena = int(args.serve_arena_gb * 1e9)
+    srv = S.Server(arena, workers=args.serve_workers, ctx=ctx)
+    t0 = srv.now()
+    ids = [srv.submit(j.workload, opts=S.make_opts(omega=j.workload.omega, precision="mixed"),
+                      arrival=t0 + j.arrival, fields=False) for j in jobs]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.concatenate([r["latency"] for r in res])
+    svc = np.array([rep["seconds"] for r in res for rep in r["reports"]])
+    makespan = max(r["finished"] for r in res) - t0
+    last_arrival = max(r["arrival"] for r in res) - t0
+    return {
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
+        "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
+        "steps": int(lat.size), "steps_per_s": float(lat.size / makespan),
+        "makespan_s": makespan, "last_arrival_s": last_arrival, "jobs": len(jobs),
+        "jobs_not_ok": sum(1 for r in res if r["status"] != 0),
+        "workers": st["workers"], "max_active": st["max_active"],
+        "arena_gb": st["arena_bytes"] / 1e9, "arena_peak_gb": st["arena_peak"] / 1e9,
+        "sample": f"{len(jobs)} jobs, Poisson rate {args.serve_rate}/s (seed 0), notched squares "
+                  f"and bars, N log-uniform 32..{args.serve_max_n} (multiple of 16), 10-60 load "
+                  f"steps each, mixed precision, default tolerances",
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -264,6 +310,11 @@ def run_ours(args):
     from paper_1511_08463_gb300 import sim as S
 
     lib = B.load()
+    if args.serve_only:
+        rec = serve_record(args, S.Context(local))
+        if rank == 0:
+            print(json.dumps({"serving": rec}), flush=True)
+        return 0
     w = W.notched_square(n=args.size)
     nsched = len(w.loads)
     W0 = min(args.warmup, nsched - 1)
@@ -390,6 +441,15 @@ def run_ours(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e!s}"[:300]}
 
+    # ---- serving leg (rank-local request loop; rank 0 reports) ---------------------------------
+    serving = None
+    n_dofs, ws_gb = 3 * sim.n_nodes, sim.workspace_bytes / 1e9
+    if args.serve_jobs > 0:
+        sim.close()  # release the 1024^2 workspace before the serving arena
+        del sim
+        torch.cuda.empty_cache()
+        serving = serve_record(args, ctx)
+
     if rank == 0:
         am_its = [r["am_iters"] for r in reps]
         line = {
@@ -399,12 +459,12 @@ def run_ours(args):
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {
                 "workload": f"notched_square_{args.size}_crossed_AT1_ORAM_omega1.5",
-                "mesh": f"{args.size}x{args.size} crossed P1", "dofs": 3 * sim.n_nodes,
+                "mesh": f"{args.size}x{args.size} crossed P1", "dofs": n_dofs,
                 "load_steps": f"{W0 + 1}-{W0 + K} of {nsched} (t up to {w.loads[-1][0]})",
                 "precision": args.precision, "parallelism": f"replicas x{world}",
                 "cuda_graphs": not args.no_graphs,
                 "l2": f"inputs larger than L2: resident state + work buffers "
-                      f"{sim.workspace_bytes / 1e9:.2f} GB per replica"},
+                      f"{ws_gb:.2f} GB per replica"},
             "clocks": clk, "gpu_launches": int(launches),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n, "steps": K,
@@ -413,6 +473,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "fp64_window": fp,
+            "serving": serving,
             "solver": {"am_iters_per_step": am_its,
                        "cg_u": sum(r["cg_iters_u"] for r in reps),
                        "cg_alpha": sum(r["cg_iters_alpha"] for r in reps),

@@ -124,6 +124,7 @@ typedef struct pf_solver_opts {
   double minres_rtol;
   int32_t use_graphs;      /* 1 (default): each PCG solve runs as one CUDA graph with a device-side
                             * loop; 0: host-driven iterations */
+  int32_t batch_workers;   /* host threads (one stream each) of pf_solve_batch; default 8 */
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step). */
@@ -150,8 +151,12 @@ const char* pf_version(void);
 pf_status pf_default_opts(pf_solver_opts* o);
 
 /* Create a context bound to CUDA device `device` (makes it current on this thread).  The
- * context allocates a small pinned host buffer; no device memory. */
+ * context owns a pool of small pinned host buffers (one per live sim, for scalar read-back); no
+ * device memory.  Sims and servers may be used from several host threads at once (one thread
+ * per sim at a time). */
 pf_status pf_ctx_create(int device, pf_ctx** out);
+/* Release the context.  Sims and servers created from it stay valid: the context is freed when
+ * the last of them is destroyed. */
 void pf_ctx_destroy(pf_ctx* ctx);
 
 /* Bytes of device workspace pf_create_mesh needs for this mesh (both precisions included; the
@@ -182,9 +187,73 @@ pf_status pf_load_step(pf_sim* sim, const pf_load* L, const pf_solver_opts* o, v
 pf_status pf_energy(pf_sim* sim, void* stream, double out[3]);
 
 /* One load step for each of n sims (loads[i] for sims[i]) with shared options; per-sim reports
- * in reps[i] (may be NULL).  The sims' work is issued concurrently; returns the worst status. */
+ * in reps[i] (may be NULL).  No counterpart in the paper (it solves one problem at a time): the
+ * steps run concurrently from o->batch_workers host threads, each on its own non-blocking stream
+ * forked from `stream` (work already queued there comes first) and joined back into it, largest
+ * meshes first.  The sims must be distinct and belong to ctx (PF_EINVAL otherwise).  Each sim's
+ * result is the same as from pf_load_step alone.  Blocks until all steps end; returns the worst
+ * status. */
 pf_status pf_solve_batch(pf_ctx* ctx, pf_sim* const* sims, const pf_load* loads, int n,
                          const pf_solver_opts* o, void* stream, pf_step_report* reps);
+
+/* ---------------------------------------------------------------------------------------------
+ * Serving: a request loop over many simulations (no counterpart in the paper, which runs one
+ * simulation at a time).  Jobs arrive over time; each is admitted, in arrival order, once its
+ * workspace (pf_workspace_bytes) fits in the free part of the caller-owned device arena, and its
+ * u, alpha, alpha_prev stay resident there until its last load step.  n_workers host threads,
+ * each with its own non-blocking CUDA stream, run load steps of the admitted jobs round robin
+ * (continuous batching: a job admitted while others run shares the device with them).  A job's
+ * results do not depend on which other jobs run beside it.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct pf_server pf_server;
+
+typedef struct pf_job {
+  pf_mesh_desc mesh;
+  pf_material material;
+  const pf_load* loads;     /* n_loads steps; copied at submission */
+  int32_t n_loads;
+  pf_solver_opts opts;
+  double arrival;           /* seconds on the server clock at which the job arrives; < 0: now */
+  /* optional caller-owned host outputs, written before the job is reported done; they must stay
+   * valid until then: final u (2*n_nodes) and alpha (n_nodes); per-step reports (n_loads); per-
+   * step latency in seconds (n_loads): end of the step minus the moment it became ready (the
+   * job's arrival for the first step, the end of the previous step otherwise), so queueing for
+   * admission and for a worker is included. */
+  double* u_out;
+  double* alpha_out;
+  pf_step_report* reports;
+  double* step_latency;
+} pf_job;
+
+typedef struct pf_job_info {
+  int32_t status;           /* worst status over the job's steps (PF_ENOMEM etc. if not admitted) */
+  int32_t steps_done;
+  double arrival, admitted, finished;  /* server clock, seconds */
+  size_t footprint;         /* arena bytes held while admitted */
+} pf_job_info;
+
+typedef struct pf_server_stats {
+  int64_t jobs_done, steps_done;
+  size_t arena_bytes, arena_peak;
+  int32_t max_active, workers;
+} pf_server_stats;
+
+/* Start a server on ctx's device.  arena: device memory of arena_bytes, 256-byte aligned,
+ * caller-owned, outliving the server.  n_workers in [1, 256].  The server clock starts here. */
+pf_status pf_server_create(pf_ctx* ctx, void* arena, size_t arena_bytes, int n_workers,
+                           pf_server** out);
+/* Seconds since pf_server_create. */
+double pf_server_now(const pf_server* s);
+/* Queue a job (thread-safe, any time).  PF_ENOMEM if its workspace exceeds the whole arena,
+ * PF_EINVAL for an invalid mesh or no load steps.  *id identifies it in pf_server_wait. */
+pf_status pf_server_submit(pf_server* s, const pf_job* job, int64_t* id);
+/* Block until job `id` is done; info may be NULL. */
+pf_status pf_server_wait(pf_server* s, int64_t id, pf_job_info* info);
+/* Block until every submitted job is done. */
+pf_status pf_server_drain(pf_server* s);
+pf_status pf_server_get_stats(pf_server* s, pf_server_stats* out);
+/* Wait for all submitted jobs, stop the workers and free the server (not the arena). */
+void pf_server_destroy(pf_server* s);
 
 /* Copy the resident state to / from host memory (FP64, node order above, u interleaved).  Any
  * pointer may be NULL to skip that field.  Synchronous.  pf_set_fields also sets the current
@@ -269,11 +338,13 @@ pf_status pf_energy_noalloc(const pf_mesh_desc* d, const pf_material* m, const p
                             const double* u, const double* alpha, double out[3], void* stream);
 
 /* ---------------------------------------------------------------------------------------------
- * Launch accounting and kernel timing (tracing support; process-wide, not thread-safe).
- * Every kernel the library launches is counted.  With timing enabled, each launch of the
+ * Launch accounting and kernel timing (tracing support; process-wide).  Every kernel the
+ * library launches is counted, exactly, from any number of host threads (a kernel inside a
+ * CUDA graph counts once per replay).  With timing enabled, each launch of the
  * selected kernel class (-1 = every class) is bracketed by two CUDA events recorded on the
  * launching stream; the measured time and the launch's algorithmic bytes (compulsory reads and
- * writes of the operator on its grid) are accumulated per class.
+ * writes of the operator on its grid) are accumulated per class.  Timing is meant for single-
+ * threaded runs: work of other threads on other streams would overlap the bracketed launches.
  * ------------------------------------------------------------------------------------------ */
 pf_status pf_prof_enable(int on, int kernel_class);
 pf_status pf_prof_reset(void);

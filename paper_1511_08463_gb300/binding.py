@@ -48,7 +48,8 @@ class pf_solver_opts(C.Structure):
                 ("mg_levels_max", C.c_int32), ("mg_degree", C.c_int32),
                 ("switch_tol", C.c_double), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int32), ("minres_maxit", C.c_int32),
-                ("minres_rtol", C.c_double), ("use_graphs", C.c_int32)]
+                ("minres_rtol", C.c_double), ("use_graphs", C.c_int32),
+                ("batch_workers", C.c_int32)]
 
 
 class pf_step_report(C.Structure):
@@ -64,6 +65,25 @@ class pf_step_report(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["energy"] = list(self.energy)
         return d
+
+
+class pf_job(C.Structure):
+    _fields_ = [("mesh", pf_mesh_desc), ("material", pf_material),
+                ("loads", C.POINTER(pf_load)), ("n_loads", C.c_int32),
+                ("opts", pf_solver_opts), ("arrival", C.c_double),
+                ("u_out", C.POINTER(C.c_double)), ("alpha_out", C.POINTER(C.c_double)),
+                ("reports", C.POINTER(pf_step_report)), ("step_latency", C.POINTER(C.c_double))]
+
+
+class pf_job_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps_done", C.c_int32), ("arrival", C.c_double),
+                ("admitted", C.c_double), ("finished", C.c_double), ("footprint", C.c_size_t)]
+
+
+class pf_server_stats(C.Structure):
+    _fields_ = [("jobs_done", C.c_int64), ("steps_done", C.c_int64),
+                ("arena_bytes", C.c_size_t), ("arena_peak", C.c_size_t),
+                ("max_active", C.c_int32), ("workers", C.c_int32)]
 
 
 _VP = C.c_void_p
@@ -98,6 +118,13 @@ _SIGS = {
     "pf_op_full_residual": (C.c_int, [_VP, C.POINTER(C.c_double), _VP]),
     "pf_energy_noalloc": (C.c_int, [C.POINTER(pf_mesh_desc), C.POINTER(pf_material),
                                     C.POINTER(pf_load), _VP, _VP, C.POINTER(C.c_double), _VP]),
+    "pf_server_create": (C.c_int, [_VP, _VP, C.c_size_t, C.c_int, C.POINTER(_VP)]),
+    "pf_server_now": (C.c_double, [_VP]),
+    "pf_server_submit": (C.c_int, [_VP, C.POINTER(pf_job), C.POINTER(C.c_int64)]),
+    "pf_server_wait": (C.c_int, [_VP, C.c_int64, C.POINTER(pf_job_info)]),
+    "pf_server_drain": (C.c_int, [_VP]),
+    "pf_server_get_stats": (C.c_int, [_VP, C.POINTER(pf_server_stats)]),
+    "pf_server_destroy": (None, [_VP]),
     "pf_prof_enable": (C.c_int, [C.c_int, C.c_int]),
     "pf_prof_reset": (C.c_int, []),
     "pf_launch_count": (C.c_int64, []),

@@ -1,6 +1,8 @@
 // Launch counting and per-class CUDA-event timing (see prof.hpp).
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -16,21 +18,26 @@ struct Pending {
   cudaEvent_t a, b;
 };
 
+// Counters are atomic so that sims driven from several host threads count correctly; the event
+// timing path (used by single-threaded measurement runs) takes a lock.
 struct State {
-  int64_t launches = 0;
-  int64_t per_class_launches[KC_COUNT] = {};
-  bool on = false;
-  int target = -1;  // -1: all classes
+  std::atomic<int64_t> launches{0};
+  std::atomic<int64_t> per_class_launches[KC_COUNT] = {};
+  std::atomic<bool> on{false};
+  std::atomic<int> target{-1};  // -1: all classes
+  std::mutex mu;                // guards pool, pending and the timing sums
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
-  cudaEvent_t open_a = nullptr;
-  bool capturing = false;
-  int open_id = -1;
   int64_t timed_launches[KC_COUNT] = {};
   double ms[KC_COUNT] = {};
   double bytes[KC_COUNT] = {};
 };
 State g;
+// per host thread: the launch currently bracketed and whether this thread is capturing a graph
+thread_local cudaEvent_t t_open_a = nullptr;
+thread_local int t_open_id = -1;
+thread_local bool t_capturing = false;
+thread_local int64_t t_captured = 0;  // launches recorded into a graph by this thread
 
 cudaEvent_t take_event() {
   if (g.pool.empty()) {
@@ -65,33 +72,46 @@ const char* BASE_NAMES[KC_BASE_COUNT] = {
 }  // namespace
 
 void prof_pre(int id, cudaStream_t s) {
-  g.launches++;
-  if (id >= 0 && id < KC_COUNT) g.per_class_launches[id]++;
-  if (g.on && !g.capturing && (g.target < 0 || g.target == id)) {
-    g.open_a = take_event();
-    g.open_id = id;
-    if (g.open_a) cudaEventRecord(g.open_a, s);
+  if (t_capturing) {  // not a launch yet: counted each time the graph replays it
+    ++t_captured;
+    return;
+  }
+  g.launches.fetch_add(1, std::memory_order_relaxed);
+  if (id >= 0 && id < KC_COUNT) g.per_class_launches[id].fetch_add(1, std::memory_order_relaxed);
+  if (g.on.load(std::memory_order_relaxed) && !t_capturing) {
+    const int tg = g.target.load(std::memory_order_relaxed);
+    if (tg < 0 || tg == id) {
+      std::lock_guard<std::mutex> lk(g.mu);
+      t_open_a = take_event();
+      t_open_id = id;
+      if (t_open_a) cudaEventRecord(t_open_a, s);
+    }
   }
 }
 
 void prof_post(int id, double bytes, cudaStream_t s) {
-  if (g.open_a && g.open_id == id) {
+  if (t_open_a && t_open_id == id) {
+    std::lock_guard<std::mutex> lk(g.mu);
     cudaEvent_t b = take_event();
     if (b) {
       cudaEventRecord(b, s);
-      g.pending.push_back(Pending{id, bytes, g.open_a, b});
+      g.pending.push_back(Pending{id, bytes, t_open_a, b});
     } else {
-      g.pool.push_back(g.open_a);
+      g.pool.push_back(t_open_a);
     }
-    g.open_a = nullptr;
-    g.open_id = -1;
+    t_open_a = nullptr;
+    t_open_id = -1;
     if (g.pending.size() >= 8192) harvest();
   }
 }
 
-void prof_add_launches(int64_t n) { g.launches += n; }
-void prof_set_capturing(bool on) { g.capturing = on; }
-int64_t prof_launches() { return g.launches; }
+void prof_add_launches(int64_t n) { g.launches.fetch_add(n, std::memory_order_relaxed); }
+void prof_set_capturing(bool on) {
+  t_capturing = on;
+  if (on) t_captured = 0;
+}
+int64_t prof_captured() { return t_captured; }
+int64_t prof_launches() { return g.launches.load(); }
 
 const char* kclass_name(int id) {
   static thread_local std::string s;
@@ -108,6 +128,7 @@ const char* kclass_name(int id) {
 extern "C" {
 
 pf_status pf_prof_enable(int on, int kernel_class) {
+  std::lock_guard<std::mutex> lk(pf::g.mu);
   pf::harvest();
   pf::g.on = on != 0;
   pf::g.target = kernel_class;
@@ -115,22 +136,24 @@ pf_status pf_prof_enable(int on, int kernel_class) {
 }
 
 pf_status pf_prof_reset(void) {
+  std::lock_guard<std::mutex> lk(pf::g.mu);
   pf::harvest();
   memset(pf::g.timed_launches, 0, sizeof pf::g.timed_launches);
   memset(pf::g.ms, 0, sizeof pf::g.ms);
   memset(pf::g.bytes, 0, sizeof pf::g.bytes);
-  memset(pf::g.per_class_launches, 0, sizeof pf::g.per_class_launches);
+  for (auto& c : pf::g.per_class_launches) c = 0;
   pf::g.launches = 0;
   return PF_OK;
 }
 
-int64_t pf_launch_count(void) { return pf::g.launches; }
+int64_t pf_launch_count(void) { return pf::g.launches.load(); }
 
 int pf_prof_class_count(void) { return pf::KC_COUNT; }
 
 pf_status pf_prof_get(int kernel_class, const char** name, int64_t* launches, int64_t* timed,
                       double* ms, double* bytes) {
   if (kernel_class < 0 || kernel_class >= pf::KC_COUNT) return PF_EINVAL;
+  std::lock_guard<std::mutex> lk(pf::g.mu);
   pf::harvest();
   if (name) *name = pf::kclass_name(kernel_class);
   if (launches) *launches = pf::g.per_class_launches[kernel_class];

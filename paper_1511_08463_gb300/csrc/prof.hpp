@@ -4,7 +4,9 @@
 // is enabled for its class, brackets it with two events recorded on the launching stream.  The
 // algorithmic bytes of each launch (compulsory reads and writes of the operator on its grid) are
 // accumulated beside the measured time so achieved bandwidth can be computed per class.
-// Process-wide state; not thread-safe (timing is meant for single-threaded measurement runs).
+// Process-wide state.  Launch counts are exact from any number of host threads; event timing
+// is thread-safe but meant for single-threaded measurement runs (concurrent work on other
+// streams would inflate the bracketed times).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,6 +29,8 @@ void prof_pre(int id, cudaStream_t s);
 // launches replayed by graphs are added here; while capturing, event timing is suspended
 void prof_add_launches(int64_t n);
 void prof_set_capturing(bool on);
+// kernels this thread recorded since prof_set_capturing(true)
+int64_t prof_captured();
 int64_t prof_launches();
 void prof_post(int id, double bytes, cudaStream_t s);
 const char* kclass_name(int id);

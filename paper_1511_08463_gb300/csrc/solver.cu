@@ -243,11 +243,59 @@ void layout(pf_sim& s, Arena& a) {
 
 inline RedSlot slot(pf_sim& s, int k) { return RedSlot{s.part, s.ticket, s.scal + k}; }
 
+}  // namespace
+
+double* pf_ctx::take_slot() {
+  std::lock_guard<std::mutex> lk(mu);
+  if (free_slots.empty()) {
+    constexpr int SLOTS = 64, SLOT_DOUBLES = 64;
+    double* p = nullptr;
+    if (cudaMallocHost(&p, SLOTS * SLOT_DOUBLES * sizeof(double)) != cudaSuccess) return nullptr;
+    chunks.push_back(p);
+    for (int k = SLOTS - 1; k >= 0; --k) free_slots.push_back(p + k * SLOT_DOUBLES);
+  }
+  double* p = free_slots.back();
+  free_slots.pop_back();
+  ++users;
+  return p;
+}
+
+static void free_ctx(pf_ctx* c) {
+  for (double* p : c->chunks) cudaFreeHost(p);
+  delete c;
+}
+
+void pf_ctx::give_slot(double* p) {
+  bool last;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    free_slots.push_back(p);
+    last = --users == 0 && closed;
+  }
+  if (last) free_ctx(this);
+}
+
+void pf_ctx::add_user() {
+  std::lock_guard<std::mutex> lk(mu);
+  ++users;
+}
+
+void pf_ctx::drop_user() {
+  bool last;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    last = --users == 0 && closed;
+  }
+  if (last) free_ctx(this);
+}
+
+namespace {
+
 pf_status read_scalars(pf_sim& s, cudaStream_t st, int k, int cnt, double* out) {
-  CU(cudaMemcpyAsync(s.ctx->host, s.scal + k, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(s.host, s.scal + k, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
-  for (int i = 0; i < cnt; ++i) out[i] = s.ctx->host[i];
+  for (int i = 0; i < cnt; ++i) out[i] = s.host[i];
   return PF_OK;
 }
 
@@ -542,7 +590,6 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   prof_set_capturing(true);
-  const int64_t l0 = prof_launches();
   precond<T>(s, cs, phys, K.r, K.z, deg);
   vec_dot<T>(cs, K.r, K.z, nd, slot(s, S_RZ1));
   cg_update_p<T>(cs, K.p, K.z, nd, s.scal + S_RZ1, s.scal + S_RZ0);
@@ -550,8 +597,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   cg_update_xr<T>(cs, K.x, K.r, K.p, K.Ap, nd, s.scal + S_RZ1, s.scal + S_PAP, slot(s, S_RR));
   cg_control(cs, h, s.scal + S_RZ1, s.scal + S_RZ0, s.scal + S_RR, s.scal + S_TOL2, s.scal + S_IT,
              s.scal + S_MAXIT);
-  const int64_t nk = prof_launches() - l0;
-  prof_add_launches(-nk);  // counted again each time the graph replays them
+  const int64_t nk = prof_captured();
   prof_set_capturing(false);
   cudaGraph_t captured;
   cudaError_t e1 = cudaStreamEndCapture(cs, &captured);
@@ -590,7 +636,7 @@ pf_status pcg_graph(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit,
   if (relres) *relres = 0.0;
   if (rr0 == 0.0) return PF_OK;
   const double tol2 = rtol * rtol * rr0;
-  double* hb = s.ctx->host;
+  double* hb = s.host;
   hb[0] = tol2;
   hb[1] = 0.0;
   hb[2] = double(maxit);
@@ -1190,70 +1236,11 @@ pf_status describe_material(const pf_material* mi, Mat* out) {
 // =============================================================================================
 // C ABI
 // =============================================================================================
-extern "C" {
-
-const char* pf_last_error(void) { return g_err.c_str(); }
-const char* pf_version(void) { return "libpf 0.1 (sm_103a)"; }
-
-pf_status pf_default_opts(pf_solver_opts* o) {
-  if (!o) return fail(PF_EINVAL, "null options");
-  memset(o, 0, sizeof *o);
-  o->algo = PF_ALGO_ORAM;
-  o->precision = PF_FP64;
-  o->omega = 1.0;
-  o->am_tol = 1e-6;
-  o->am_maxit = 2000;
-  o->u_rtol = 1e-8;
-  o->inner_rtol = 1e-4;
-  o->cg_maxit = 2000;
-  o->rs_rtol = 1e-8;
-  o->rs_maxit = 100;
-  o->alpha_cg_rtol = 1e-6;
-  o->zeta = 1e-10;
-  o->mg_levels_max = 0;
-  o->mg_degree = 2;
-  o->switch_tol = 1e-2;
-  o->newton_rtol = 1e-8;
-  o->newton_maxit = 30;
-  o->minres_maxit = 500;
-  o->minres_rtol = 1e-6;
-  o->use_graphs = 1;
-  return PF_OK;
-}
-
-pf_status pf_ctx_create(int device, pf_ctx** out) {
-  if (!out) return fail(PF_EINVAL, "null output");
-  CU(cudaSetDevice(device));
-  pf_ctx* c = new (std::nothrow) pf_ctx;
-  if (!c) return fail(PF_ENOMEM, "host allocation failed");
-  c->device = device;
-  cudaError_t e = cudaMallocHost(&c->host, 64 * sizeof(double));
-  if (e != cudaSuccess) {
-    delete c;
-    return fail(PF_ECUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
-  }
-  *out = c;
-  return PF_OK;
-}
-
-void pf_ctx_destroy(pf_ctx* c) {
-  if (!c) return;
-  if (c->host) cudaFreeHost(c->host);
-  delete c;
-}
-
-size_t pf_workspace_bytes(const pf_mesh_desc* d, int precision) {
-  (void)precision;
-  if (validate(d) != PF_OK) return 0;
-  pf_sim s;
-  s.desc = *d;
-  Arena a{nullptr, 0, 0, true};
-  layout(s, a);
-  return a.off + 256;
-}
-
-pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_bytes,
-                         pf_sim** out) {
+namespace pf {
+// Build a sim in caller-given workspace; every device operation is ordered on `st` and finished
+// when this returns (no device-wide synchronization, so other streams keep running).
+pf_status create_sim(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_bytes,
+                     cudaStream_t st, pf_sim** out) {
   if (!ctx || !out) return fail(PF_EINVAL, "null argument");
   TRY(validate(d));
   if (!ws) return fail(PF_EINVAL, "null workspace");
@@ -1264,6 +1251,11 @@ pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws
   pf_sim* s = new (std::nothrow) pf_sim;
   if (!s) return fail(PF_ENOMEM, "host allocation failed");
   s->ctx = ctx;
+  s->host = ctx->take_slot();
+  if (!s->host) {
+    delete s;
+    return fail(PF_ECUDA, "cudaMallocHost failed");
+  }
   s->desc = *d;
   Arena a{static_cast<char*>(ws), ws_bytes, 0, false};
   layout(*s, a);
@@ -1296,19 +1288,110 @@ pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws
       if (d->pin_comp[k] == 2 && d->pin_x2[k] == X2 && d->pin_y2[k] == Y2) al[node] = d->pin_load[k];
   }
   std::vector<float> al32(al.begin(), al.end());
-  cudaError_t e1 = cudaMemset(s->u, 0, 2 * (size_t)g.n * sizeof(double));
-  cudaError_t e2 = cudaMemcpy(s->alpha, al.data(), g.n * sizeof(double), cudaMemcpyHostToDevice);
-  cudaError_t e3 = cudaMemcpy(s->alpha_prev, al.data(), g.n * sizeof(double), cudaMemcpyHostToDevice);
-  cudaError_t e4 = cudaMemcpy(s->alpha32, al32.data(), g.n * sizeof(float), cudaMemcpyHostToDevice);
-  cudaError_t e5 = cudaMemset(s->ticket, 0, 64 * sizeof(unsigned));
-  cudaError_t e6 = cudaMemset(s->eig, 0, (size_t)g.ny * elems_per_cell(g.kind) * sizeof(double));
-  cudaError_t e7 = cudaDeviceSynchronize();
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+  cudaError_t e1 = cudaMemsetAsync(s->u, 0, 2 * (size_t)g.n * sizeof(double), st);
+  cudaError_t e2 = cudaMemcpyAsync(s->alpha, al.data(), g.n * sizeof(double), h2d, st);
+  cudaError_t e3 = cudaMemcpyAsync(s->alpha_prev, al.data(), g.n * sizeof(double), h2d, st);
+  cudaError_t e4 = cudaMemcpyAsync(s->alpha32, al32.data(), g.n * sizeof(float), h2d, st);
+  cudaError_t e5 = cudaMemsetAsync(s->ticket, 0, 64 * sizeof(unsigned), st);
+  cudaError_t e6 =
+      cudaMemsetAsync(s->eig, 0, (size_t)g.ny * elems_per_cell(g.kind) * sizeof(double), st);
+  cudaError_t e7 = cudaStreamSynchronize(st);  // the host vectors above are read until here
   for (cudaError_t e : {e1, e2, e3, e4, e5, e6, e7})
     if (e != cudaSuccess) {
       delete s;
       return fail(PF_ECUDA, "initial state upload: %s", cudaGetErrorString(e));
     }
   *out = s;
+  return PF_OK;
+}
+
+// Copy the resident fields to host memory, ordered on `st`; synchronous.
+pf_status fields_to_host(pf_sim* s, cudaStream_t st, double* u, double* alpha,
+                         double* alpha_prev) {
+  const size_t n = s->lv[0].g.n;
+  const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+  if (u) CU(cudaMemcpyAsync(u, s->u, 2 * n * sizeof(double), d2h, st));
+  if (alpha) CU(cudaMemcpyAsync(alpha, s->alpha, n * sizeof(double), d2h, st));
+  if (alpha_prev) CU(cudaMemcpyAsync(alpha_prev, s->alpha_prev, n * sizeof(double), d2h, st));
+  CU(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+}  // namespace pf
+
+extern "C" {
+
+const char* pf_last_error(void) { return g_err.c_str(); }
+const char* pf_version(void) { return "libpf 0.1 (sm_103a)"; }
+
+pf_status pf_default_opts(pf_solver_opts* o) {
+  if (!o) return fail(PF_EINVAL, "null options");
+  memset(o, 0, sizeof *o);
+  o->algo = PF_ALGO_ORAM;
+  o->precision = PF_FP64;
+  o->omega = 1.0;
+  o->am_tol = 1e-6;
+  o->am_maxit = 2000;
+  o->u_rtol = 1e-8;
+  o->inner_rtol = 1e-4;
+  o->cg_maxit = 2000;
+  o->rs_rtol = 1e-8;
+  o->rs_maxit = 100;
+  o->alpha_cg_rtol = 1e-6;
+  o->zeta = 1e-10;
+  o->mg_levels_max = 0;
+  o->mg_degree = 2;
+  o->switch_tol = 1e-2;
+  o->newton_rtol = 1e-8;
+  o->newton_maxit = 30;
+  o->minres_maxit = 500;
+  o->minres_rtol = 1e-6;
+  o->use_graphs = 1;
+  o->batch_workers = 8;
+  return PF_OK;
+}
+
+pf_status pf_ctx_create(int device, pf_ctx** out) {
+  if (!out) return fail(PF_EINVAL, "null output");
+  CU(cudaSetDevice(device));
+  pf_ctx* c = new (std::nothrow) pf_ctx;
+  if (!c) return fail(PF_ENOMEM, "host allocation failed");
+  c->device = device;
+  double* probe = c->take_slot();  // allocate the first chunk now so errors surface here
+  if (!probe) {
+    delete c;
+    return fail(PF_ECUDA, "cudaMallocHost failed");
+  }
+  c->give_slot(probe);
+  *out = c;
+  return PF_OK;
+}
+
+void pf_ctx_destroy(pf_ctx* c) {
+  if (!c) return;
+  bool now;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->closed = true;
+    now = c->users == 0;
+  }
+  if (now) free_ctx(c);
+}
+
+size_t pf_workspace_bytes(const pf_mesh_desc* d, int precision) {
+  (void)precision;
+  if (validate(d) != PF_OK) return 0;
+  pf_sim s;
+  s.desc = *d;
+  Arena a{nullptr, 0, 0, true};
+  layout(s, a);
+  return a.off + 256;
+}
+
+pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_bytes,
+                         pf_sim** out) {
+  TRY(pf::create_sim(ctx, d, ws, ws_bytes, nullptr, out));
+  CU(cudaDeviceSynchronize());
   return PF_OK;
 }
 
@@ -1390,17 +1473,6 @@ pf_status pf_energy(pf_sim* s, void* stream, double out[3]) {
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   return energy_now(*s, static_cast<cudaStream_t>(stream), out);
-}
-
-pf_status pf_solve_batch(pf_ctx* ctx, pf_sim* const* sims, const pf_load* loads, int n,
-                         const pf_solver_opts* o, void* stream, pf_step_report* reps) {
-  if (!ctx || (n > 0 && (!sims || !loads))) return fail(PF_EINVAL, "null argument");
-  pf_status worst = PF_OK;
-  for (int i = 0; i < n; ++i) {
-    pf_status st = pf_load_step(sims[i], &loads[i], o, stream, reps ? &reps[i] : nullptr);
-    if (st > worst) worst = st;
-  }
-  return worst;
 }
 
 pf_status pf_get_fields(pf_sim* s, double* u, double* alpha, double* alpha_prev) {

@@ -2,14 +2,28 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "kernels.cuh"
 
+// One per GPU.  Owns a pool of small pinned host buffers (one per live sim, for scalar
+// read-back), grown in chunks and released only with the context, so that creating and
+// destroying sims never calls cudaFreeHost (which may synchronize the device) while other
+// sims run.  Sims and servers hold a reference: pf_ctx_destroy frees the context once the last
+// of them is gone, whatever the order in which the caller releases them.
 struct pf_ctx {
-  int device;
-  double* host;  // pinned scratch for scalar read-back (64 doubles)
+  int device = 0;
+  std::mutex mu;
+  std::vector<double*> chunks;      // cudaMallocHost blocks
+  std::vector<double*> free_slots;  // 64-double slots not in use
+  int users = 0;                    // live sims and servers
+  bool closed = false;              // pf_ctx_destroy was called
+  double* take_slot();              // also registers a user
+  void give_slot(double* p);        // also unregisters it; may free the context
+  void add_user();
+  void drop_user();                 // may free the context
 };
 
 namespace pf {
@@ -56,6 +70,10 @@ enum Slot {
 void set_error_message(const char* msg);
 pf_status describe_mesh(const pf_mesh_desc* d, Grid* g);      // validate + level-0 grid
 pf_status describe_material(const pf_material* m, Mat* out);  // validate + kernel constants
+// stream-ordered variants of pf_create_mesh and pf_get_fields (no device-wide synchronization)
+pf_status create_sim(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_bytes,
+                     cudaStream_t st, pf_sim** out);
+pf_status fields_to_host(pf_sim* s, cudaStream_t st, double* u, double* alpha, double* alpha_prev);
 
 }  // namespace pf
 
@@ -107,7 +125,9 @@ struct pf_sim {
   cudaGraphExec_t cg_exec[2][2] = {};
   int cg_body_kernels[2][2] = {};
   int cg_deg[2][2] = {};
+  double* host = nullptr;  // pinned read-back slot from the context's pool
   ~pf_sim() {
+    if (host && ctx) ctx->give_slot(host);
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b) {
         if (cg_exec[a][b]) cudaGraphExecDestroy(cg_exec[a][b]);

@@ -234,3 +234,89 @@ def solve_batch(sims, loads, opts=None, stream=None, ctx: Context | None = None)
     o = opts or make_opts()
     st = lib.pf_solve_batch(ctx.h, hs, ls, n, C.byref(o), C.c_void_p(_stream(stream)), reps)
     return st, [r.as_dict() for r in reps]
+
+
+class Server:
+    """Serving loop of libpf (pf_server_*): jobs arrive over time, are admitted by HBM footprint
+    into one device arena and advance one load step at a time on `workers` host threads, each
+    with its own CUDA stream.  Argument marshalling only."""
+
+    def __init__(self, arena_bytes: int, workers: int = 8, ctx: Context | None = None):
+        self.lib = B.load()
+        self.ctx = ctx or Context(0)
+        self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8,
+                                 device=f"cuda:{self.ctx.device}")
+        aligned = (self.arena.data_ptr() + 255) & ~255
+        h = C.c_void_p()
+        B.check(self.lib.pf_server_create(self.ctx.h, C.c_void_p(aligned), arena_bytes, workers,
+                                          C.byref(h)))
+        self.h = h
+        self._jobs = {}
+
+    @staticmethod
+    def footprint(w) -> int:
+        return B.load().pf_workspace_bytes(C.byref(mesh_desc(w)), B.PF_FP64)
+
+    def now(self) -> float:
+        return self.lib.pf_server_now(self.h)
+
+    def submit(self, w, loads=None, opts=None, arrival: float = -1.0, fields: bool = True) -> int:
+        """Queue workload w with its load steps (default w.loads); arrival in seconds on the
+        server clock (< 0: now).  Returns the job id."""
+        loads = list(w.loads if loads is None else loads)
+        n = w.n_nodes()
+        keep = {
+            "loads": (B.pf_load * len(loads))(*[B.pf_load(t, dT) for (t, dT) in loads]),
+            "reports": (B.pf_step_report * len(loads))(),
+            "latency": (C.c_double * len(loads))(),
+            "u": (C.c_double * (2 * n))() if fields else None,
+            "alpha": (C.c_double * n)() if fields else None,
+            "n": n,
+        }
+        job = B.pf_job()
+        job.mesh = mesh_desc(w)
+        job.material = material(w)
+        job.loads = C.cast(keep["loads"], C.POINTER(B.pf_load))
+        job.n_loads = len(loads)
+        job.opts = opts or make_opts(omega=w.omega)
+        job.arrival = arrival
+        dp = C.POINTER(C.c_double)
+        job.u_out = C.cast(keep["u"], dp) if fields else dp()
+        job.alpha_out = C.cast(keep["alpha"], dp) if fields else dp()
+        job.reports = C.cast(keep["reports"], C.POINTER(B.pf_step_report))
+        job.step_latency = C.cast(keep["latency"], dp)
+        jid = C.c_int64()
+        B.check(self.lib.pf_server_submit(self.h, C.byref(job), C.byref(jid)))
+        self._jobs[jid.value] = keep
+        return jid.value
+
+    def wait(self, jid: int) -> dict:
+        info = B.pf_job_info()
+        B.check(self.lib.pf_server_wait(self.h, jid, C.byref(info)))
+        k = self._jobs[jid]
+        out = {f: getattr(info, f) for f, _ in info._fields_}
+        out["reports"] = [r.as_dict() for r in k["reports"]][: info.steps_done]
+        out["latency"] = np.array(k["latency"][: info.steps_done])
+        if k["u"] is not None:
+            out["u"] = np.array(k["u"]).reshape(k["n"], 2)
+            out["alpha"] = np.array(k["alpha"])
+        return out
+
+    def drain(self):
+        B.check(self.lib.pf_server_drain(self.h))
+
+    def stats(self) -> dict:
+        s = B.pf_server_stats()
+        B.check(self.lib.pf_server_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
