@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--algo", choices=["ORAM", "ORAM_N"], default="ORAM",
+                    help="ORAM (Algorithm 2) or ORAM-N (Algorithm 3)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
@@ -321,7 +323,7 @@ def run_ours(args):
     K = max(1, min(args.steps, nsched - W0))
     ctx = S.Context(local)
     sim = S.Sim(w, ctx)
-    opts = S.make_opts(algo="ORAM", omega=w.omega, precision=args.precision,
+    opts = S.make_opts(algo=args.algo, omega=w.omega, precision=args.precision,
                        use_graphs=0 if args.no_graphs else 1)
     log(args, f"[rank {rank}] nodes {sim.n_nodes} levels {sim.levels} workspace "
               f"{sim.workspace_bytes / 1e9:.2f} GB; warm-up {W0} steps")
@@ -335,7 +337,7 @@ def run_ours(args):
     # CUDA events on the launching stream (events cannot bracket single launches in a graph)
     lib.pf_prof_reset()
     lib.pf_prof_enable(1, -1)
-    popts = S.make_opts(algo="ORAM", omega=w.omega, precision=args.precision, use_graphs=0)
+    popts = S.make_opts(algo=args.algo, omega=w.omega, precision=args.precision, use_graphs=0)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     sim.load_step(*w.loads[W0], popts, allow_notconv=True)
@@ -416,7 +418,7 @@ def run_ours(args):
     KF = min(args.fp64_steps, K)
     if KF > 0:
         sim.set_fields(*snap)
-        o64 = S.make_opts(algo="ORAM", omega=w.omega, precision="fp64",
+        o64 = S.make_opts(algo=args.algo, omega=w.omega, precision="fp64",
                           use_graphs=0 if args.no_graphs else 1)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,7 +460,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {
-                "workload": f"notched_square_{args.size}_crossed_AT1_ORAM_omega1.5",
+                "workload": f"notched_square_{args.size}_crossed_AT1_{args.algo}_omega1.5",
                 "mesh": f"{args.size}x{args.size} crossed P1", "dofs": n_dofs,
                 "load_steps": f"{W0 + 1}-{W0 + K} of {nsched} (t up to {w.loads[-1][0]})",
                 "precision": args.precision, "parallelism": f"replicas x{world}",
@@ -474,7 +476,10 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fp64_window": fp,
             "serving": serving,
-            "solver": {"am_iters_per_step": am_its,
+            "solver": {"algo": args.algo, "am_iters_per_step": am_its,
+                       "newton_iters_per_step": [r["newton_iters"] for r in reps],
+                       "seconds_per_step": [round(r["seconds"], 3) for r in reps],
+                       "minres_iters": sum(r["krylov_iters_newton"] for r in reps),
                        "cg_u": sum(r["cg_iters_u"] for r in reps),
                        "cg_alpha": sum(r["cg_iters_alpha"] for r in reps),
                        "rs_iters": sum(r["rs_iters"] for r in reps),

@@ -97,12 +97,19 @@ typedef struct pf_load {
 } pf_load;
 
 /* Solver options.  Defaults from pf_default_opts().  Tolerances:
- *   am_tol: stop ORAM when max|alpha^k - alpha^{k-1}| <= am_tol and
- *           max|u^k - u^{k-1}| <= am_tol * max|u^k| (Section 1.2 stopping criterion, see design
- *           notes for the second part).
- *   u_rtol: u-subproblem FP64 residual <= u_rtol * (first residual of the load step).
+ *   am_tol: stop ORAM when max|alpha^k - alpha^{k-1}| <= am_tol (the damage-change criterion
+ *           of Section 1.2) and max|u^k - u^{k-1}| <= am_tol * max|u^k| (the same test on the
+ *           displacement, so that a step whose damage does not move still solves for u).
+ *   u_rtol: u-subproblem FP64 residual <= u_rtol * (largest residual seen in the load step).
  *   inner_rtol: relative tolerance of each inner FP32 CG solve (PF_MIXED).
- *   rs_rtol: damage subproblem ||Phi||_2 <= rs_rtol * ||g0||_2 (Algorithm 4 termination).
+ *   rs_rtol: damage subproblem ||Phi||_2 <= rs_rtol * (largest ||Phi||_2 seen in the load step)
+ *           (Algorithm 4 termination).
+ *   am_forcing, am_forcing_max: inexact subproblem solves.  In AM iteration k the two
+ *           tolerances above are raised to f_k = min(am_forcing_max, am_forcing * dalpha_{k-1})
+ *           (dalpha_0 = infinity), so the subproblems are solved loosely while the damage moves
+ *           a lot and to u_rtol / rs_rtol as the iteration converges; the am_tol test is
+ *           then accepted only in an iteration whose predecessor already met it (so its
+ *           tolerances were at most am_forcing * am_tol).  0 (default): exact solves. 
  *   alpha_cg_rtol: relative tolerance of the reduced Newton solves inside Algorithm 4.
  *   zeta: zero tolerance of the active set (eq. reducedis).
  *   switch_tol: ORAM-N switches to Newton when ||Phi^k|| / ||Phi^0|| <= switch_tol (Alg. 3).
@@ -117,7 +124,10 @@ typedef struct pf_solver_opts {
   double rs_rtol;
   int32_t rs_maxit;
   double alpha_cg_rtol, zeta;
-  int32_t mg_levels_max;   /* 0 = as many as the mesh allows; 1 = Jacobi-preconditioned CG */
+  int32_t mg_levels_max;   /* multigrid levels used (0 = all the mesh allows; 1 = CG with the
+                            * l1-Jacobi Chebyshev smoother as preconditioner).  A coarsest level in
+                            * use that is not the mesh's coarsest (dense solve) is smoothed with
+                            * 8 * mg_degree steps. */
   int32_t mg_degree;       /* Chebyshev smoothing steps per pre/post smoothing */
   double switch_tol, newton_rtol;
   int32_t newton_maxit, minres_maxit;
@@ -125,6 +135,7 @@ typedef struct pf_solver_opts {
   int32_t use_graphs;      /* 1 (default): each PCG solve runs as one CUDA graph with a device-side
                             * loop; 0: host-driven iterations */
   int32_t batch_workers;   /* host threads (one stream each) of pf_solve_batch; default 8 */
+  double am_forcing, am_forcing_max;
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step). */

@@ -119,12 +119,16 @@ struct pf_sim {
   size_t ws_used = 0;
   bool busy = false;
   // CUDA graphs holding one whole PCG solve each (device-side while loop), per operator
-  // (elastic, damage) and precision (FP32, FP64); rebuilt if the smoothing degree changes
+  // (elastic, damage) and precision (FP32, FP64); rebuilt if the smoothing degree or the number of
+  // levels in use changes
   bool use_graphs = true;
   cudaGraph_t cg_graph[2][2] = {};
   cudaGraphExec_t cg_exec[2][2] = {};
   int cg_body_kernels[2][2] = {};
   int cg_deg[2][2] = {};
+  int cg_nl[2][2] = {};
+  // multigrid levels used by the solves (pf_solver_opts.mg_levels_max; all by default)
+  int nl_active = 1;
   double* host = nullptr;  // pinned read-back slot from the context's pool
   ~pf_sim() {
     if (host && ctx) ctx->give_slot(host);
