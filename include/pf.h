@@ -136,6 +136,9 @@ typedef struct pf_solver_opts {
                             * loop; 0: host-driven iterations */
   int32_t batch_workers;   /* host threads (one stream each) of pf_solve_batch; default 8 */
   double am_forcing, am_forcing_max;
+  int32_t mg_tail;         /* 1 (default): in FP32 V-cycles, the coarse levels that fit in one
+                            * SM's shared memory run as a single thread block; 0: one grid per
+                            * step on every level */
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step). */

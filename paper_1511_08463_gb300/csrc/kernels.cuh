@@ -95,6 +95,34 @@ template <class T>
 void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0);
 template <class T>
 void coarse_invert(cudaStream_t s, int n, const T* L, T* Ainv);  // explicit inverse from L
+// ---- the coarse end of a V-cycle in one thread block (tail.cu) ---------------------------------
+constexpr int MAX_TAIL = 8;          // levels the single-block kernel can hold
+constexpr int TAIL_THREADS = 1024;
+constexpr int TAIL_MAX_NODES = 1200;  // largest level a tail starts on, unless it holds them all
+struct TailLevel {
+  Grid g;
+  Consts<float> cs;
+  const float* coef;     // elastic abar_T or damage weight w_T per element (device)
+  const float* dinv;     // inverse l1 diagonal (device)
+  const uint8_t* excl;   // damage: excluded nodes (device); elastic: null
+  int ox, oxn, ob, od, odi, oc, oe;  // shared-memory offsets, in floats (oe: flag bytes)
+};
+struct TailArgs {
+  int nl, deg, dense, coarse_steps;  // levels in the tail; smoothing steps; dense coarsest?
+  int orec;                          // shared-memory offset of the element records, in floats
+  const float* Ainv;                 // coarsest inverse (dense)
+  const float* b_in;                 // right-hand side on the tail's first level (device)
+  float* x_out;                      // V-cycle result on that level (device)
+  TailLevel L[MAX_TAIL];
+};
+size_t tail_smem_limit();  // dynamic shared memory available to the tail kernel (0: none)
+void tail_vcycle(cudaStream_t s, int ncomp, const TailArgs& a, size_t smem);
+
+// Both steps: in shared memory when the packed factor fits, else the two kernels above.
+// A (n x n, row-major, overwritten), diag0 (pivot floor), Ainv (n x n).
+constexpr int COARSE_WARPS = 8;  // columns of the inverse per block
+template <class T>
+void coarse_factor_invert(cudaStream_t s, int n, T* A, const T* diag0, T* Ainv);
 template <class T>
 void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x);  // x = Ainv b
 

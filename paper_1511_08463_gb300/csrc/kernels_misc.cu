@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include "kernels.cuh"
+#include "mg_core.cuh"
 
 namespace pf {
 
@@ -21,63 +22,69 @@ static inline unsigned rblocks(size_t n) {
 // ---------------------------------------------------------------------------------------------
 template <class T>
 __global__ void k_fill(T* y, T v, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = v;
 }
 template <class T>
 void vec_fill(cudaStream_t s, T* y, T v, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_fill<<<nblocks(n), RED_THREADS, 0, s>>>(y, v, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_fill<T>, nblocks(n), RED_THREADS, 0, s, y, v, n));
 }
 template void vec_fill<double>(cudaStream_t, double*, double, size_t);
 template void vec_fill<float>(cudaStream_t, float*, float, size_t);
 
 template <class TO, class TI>
 __global__ void k_convert(TO* y, const TI* x, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = TO(x[i]);
 }
 template <class TO, class TI>
 void vec_convert(cudaStream_t s, TO* y, const TI* x, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_convert<TO, TI><<<nblocks(n), RED_THREADS, 0, s>>>(y, x, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_convert<TO, TI>, nblocks(n), RED_THREADS, 0, s, y, x, n));
 }
 template void vec_convert<float, double>(cudaStream_t, float*, const double*, size_t);
 template void vec_convert<double, float>(cudaStream_t, double*, const float*, size_t);
 template void vec_convert<double, double>(cudaStream_t, double*, const double*, size_t);
 
 __global__ void k_add_f32_to_f64(double* x, const float* d, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] += (double)d[i];
 }
 void vec_add_f32_to_f64(cudaStream_t s, double* x, const float* d, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_add_f32_to_f64<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_add_f32_to_f64, nblocks(n), RED_THREADS, 0, s, x, d, n));
 }
 
 template <class T>
 __global__ void k_add(T* x, const T* d, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] += d[i];
 }
 template <class T>
 void vec_add(cudaStream_t s, T* x, const T* d, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_add<<<nblocks(n), RED_THREADS, 0, s>>>(x, d, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_add<T>, nblocks(n), RED_THREADS, 0, s, x, d, n));
 }
 template void vec_add<double>(cudaStream_t, double*, const double*, size_t);
 template void vec_add<float>(cudaStream_t, float*, const float*, size_t);
 
 template <class T>
 __global__ void k_mul(T* z, const T* a, const T* b, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) z[i] = a[i] * b[i];
 }
 template <class T>
 void vec_mul(cudaStream_t s, T* z, const T* a, const T* b, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_mul<<<nblocks(n), RED_THREADS, 0, s>>>(z, a, b, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_mul<T>, nblocks(n), RED_THREADS, 0, s, z, a, b, n));
 }
 template void vec_mul<double>(cudaStream_t, double*, const double*, const double*, size_t);
 template void vec_mul<float>(cudaStream_t, float*, const float*, const float*, size_t);
 
 template <class T>
 __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
+  pdl_enter();
   T v[1] = {T(0)};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
@@ -86,7 +93,7 @@ __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
 }
 template <class T>
 void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_dot<<<rblocks(n), RED_THREADS, 0, s>>>(x, y, n, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_dot<T>, rblocks(n), RED_THREADS, 0, s, x, y, n, slot));
 }
 template void vec_dot<double>(cudaStream_t, const double*, const double*, size_t, RedSlot);
 template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, RedSlot);
@@ -94,6 +101,7 @@ template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, R
 template <class T>
 __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
                         const double* pAp, RedSlot slot) {
+  pdl_enter();
   __shared__ T sa;  // step length computed once per block
   if (threadIdx.x == 0) sa = T(*rz / *pAp);
   __syncthreads();
@@ -111,7 +119,7 @@ __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const dou
 template <class T>
 void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
                   const double* pAp, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_cg_xr<<<rblocks(n), RED_THREADS, 0, s>>>(x, r, p, Ap, n, rz, pAp, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_cg_xr<T>, rblocks(n), RED_THREADS, 0, s, x, r, p, Ap, n, rz, pAp, slot));
 }
 template void cg_update_xr<double>(cudaStream_t, double*, double*, const double*, const double*,
                                    size_t, const double*, const double*, RedSlot);
@@ -120,6 +128,7 @@ template void cg_update_xr<float>(cudaStream_t, float*, float*, const float*, co
 
 template <class T>
 __global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const double* rz_old) {
+  pdl_enter();
   __shared__ T sb;  // conjugation coefficient computed once per block
   // beta = 0 (first iteration: *rz_old == 0, or no old value given) means p = z, and p is not
   // read (it may hold stale values)
@@ -132,7 +141,7 @@ __global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const d
 template <class T>
 void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
                  const double* rz_old) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_cg_p<<<nblocks(n), RED_THREADS, 0, s>>>(p, z, n, rz_new, rz_old));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_cg_p<T>, nblocks(n), RED_THREADS, 0, s, p, z, n, rz_new, rz_old));
 }
 template void cg_update_p<double>(cudaStream_t, double*, const double*, size_t, const double*,
                                   const double*);
@@ -143,6 +152,7 @@ template void cg_update_p<float>(cudaStream_t, float*, const float*, size_t, con
 // the device whether the while-loop of the graph runs again.
 __global__ void k_cg_control(cudaGraphConditionalHandle h, double* rz_new, double* rz_old,
                              const double* rr, const double* tol2, double* it, const double* maxit) {
+  pdl_enter();
   *rz_old = *rz_new;
   double k = *it + 1.0;
   *it = k;
@@ -153,11 +163,12 @@ __global__ void k_cg_control(cudaGraphConditionalHandle h, double* rz_new, doubl
 void cg_control(cudaStream_t s, cudaGraphConditionalHandle h, double* rz_new, double* rz_old,
                 const double* rr, const double* tol2, double* it, const double* maxit) {
   PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s,
-            k_cg_control<<<1, 1, 0, s>>>(h, rz_new, rz_old, rr, tol2, it, maxit));
+            pdl_launch(k_cg_control, 1, 1, 0, s, h, rz_new, rz_old, rr, tol2, it, maxit));
 }
 
 // over-relaxation of u (Algorithm 2): prescribed dofs have xt == u, so they do not move
 __global__ void k_relax_u(double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -170,7 +181,7 @@ __global__ void k_relax_u(double* u, const double* xt, double omega, size_t n2, 
   block_reduce_finalize<2, true>(v, slot);
 }
 void relax_u(cudaStream_t s, double* u, const double* xt, double omega, size_t n2, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_relax_u<<<rblocks(n2), RED_THREADS, 0, s>>>(u, xt, omega, n2, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_relax_u, rblocks(n2), RED_THREADS, 0, s, u, xt, omega, n2, slot));
 }
 
 __device__ __forceinline__ double upper_of(const Grid& g, int node, double lo) {
@@ -182,6 +193,7 @@ __device__ __forceinline__ double upper_of(const Grid& g, int node, double lo) {
 // largest w with lo <= alpha + w (at - alpha) <= hi at every node: out[0] = -w*
 __global__ void k_omega_star(Grid g, const double* alpha, const double* at, const double* lo,
                              RedSlot slot) {
+  pdl_enter();
   double v[1] = {-INFINITY};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
     double a = alpha[i], d = at[i] - a;
@@ -195,11 +207,12 @@ __global__ void k_omega_star(Grid g, const double* alpha, const double* at, cons
 }
 void omega_star(cudaStream_t s, const Grid& g, const double* alpha, const double* at,
                 const double* lo, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_omega_star<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_omega_star, rblocks(g.n), RED_THREADS, 0, s, g, alpha, at, lo, slot));
 }
 
 __global__ void k_relax_alpha(Grid g, double* alpha, const double* at, const double* lo, double w,
                               float* alpha32, RedSlot slot) {
+  pdl_enter();
   double v[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
     double a = alpha[i];
@@ -213,10 +226,11 @@ __global__ void k_relax_alpha(Grid g, double* alpha, const double* at, const dou
 }
 void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at, const double* lo,
                  double w, float* alpha32, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_relax_alpha<<<rblocks(g.n), RED_THREADS, 0, s>>>(g, alpha, at, lo, w, alpha32, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_relax_alpha, rblocks(g.n), RED_THREADS, 0, s, g, alpha, at, lo, w, alpha32, slot));
 }
 
 __global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.nv) return;  // only vertices lie on edges; pins checked below for all nodes
   int X2, Y2;
@@ -229,6 +243,7 @@ __global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
   }
 }
 __global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
+  pdl_enter();
   for (int k = 0; k < g.npins; ++k) {
     if (g.pin_comp[k] > 1) continue;
     int X2 = g.pin_x2[k], Y2 = g.pin_y2[k], node;
@@ -238,12 +253,13 @@ __global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
   }
 }
 void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_lift<<<nblocks(g.nv), RED_THREADS, 0, s>>>(g, u, t, ld));
-  if (g.npins > 0) PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_lift_pins<<<1, 1, 0, s>>>(g, u, t, ld));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_lift, nblocks(g.nv), RED_THREADS, 0, s, g, u, t, ld));
+  if (g.npins > 0) PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_lift_pins, 1, 1, 0, s, g, u, t, ld));
 }
 
 template <class T>
 __global__ void k_mask_fixed(Grid g, T* v, int ncomp) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int X2, Y2;
@@ -257,7 +273,7 @@ __global__ void k_mask_fixed(Grid g, T* v, int ncomp) {
 }
 template <class T>
 void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_mask_fixed<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, v, ncomp));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_mask_fixed<T>, nblocks(g.n), RED_THREADS, 0, s, g, v, ncomp));
 }
 template void mask_fixed<double>(cudaStream_t, const Grid&, double*, int);
 template void mask_fixed<float>(cudaStream_t, const Grid&, float*, int);
@@ -265,26 +281,10 @@ template void mask_fixed<float>(cudaStream_t, const Grid&, float*, int);
 // ---------------------------------------------------------------------------------------------
 // element-wise kernels: one thread per cell
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cell_nodes(const Grid& g, int ci, int cj, int t, int& n0, int& n1,
-                                           int& n2) {
-  int v00 = cj * (g.nx + 1) + ci, v10 = v00 + 1, v01 = v00 + g.nx + 1, v11 = v01 + 1;
-  if (g.kind == CROSSED) {
-    int c = g.nv + cj * g.nx + ci;
-    if (t == 0) { n0 = v00; n1 = v10; n2 = c; }
-    else if (t == 1) { n0 = v10; n1 = v11; n2 = c; }
-    else if (t == 2) { n0 = v11; n1 = v01; n2 = c; }
-    else { n0 = v01; n1 = v00; n2 = c; }
-  } else {
-    if (t == 0) { n0 = v00; n1 = v10; n2 = v11; }
-    else { n0 = v00; n1 = v11; n2 = v01; }
-  }
-}
-
-__device__ __forceinline__ int gxr(int kind, int t, int k) { return gx(kind, t, k); }
-__device__ __forceinline__ int gyr(int kind, int t, int k) { return gy(kind, t, k); }
 
 template <class T>
 __global__ void k_elastic_coef(Grid g, Mat m, const T* alpha, T* coef) {
+  pdl_enter();
   int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= g.ncell) return;
   int cj = cell / g.nx, ci = cell - cj * g.nx;
@@ -297,7 +297,7 @@ __global__ void k_elastic_coef(Grid g, Mat m, const T* alpha, T* coef) {
 }
 template <class T>
 void elastic_coef(cudaStream_t s, const Grid& g, const Mat& m, const T* alpha, T* coef) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_elastic_coef<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, alpha, coef));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_elastic_coef<T>, nblocks(g.ncell), RED_THREADS, 0, s, g, m, alpha, coef));
 }
 template void elastic_coef<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void elastic_coef<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -321,6 +321,7 @@ __device__ __forceinline__ void strain_of(const Grid& g, int t, const double* u,
 
 __global__ void k_damage_q(Grid g, Mat m, const double* u, const double* eig, double* q,
                            double* w64, float* w32) {
+  pdl_enter();
   int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= g.ncell) return;
   int cj = cell / g.nx, ci = cell - cj * g.nx;
@@ -343,11 +344,12 @@ __global__ void k_damage_q(Grid g, Mat m, const double* u, const double* eig, do
 }
 void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
               double* q, double* w64, float* w32) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_damage_q<<<nblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, eig, q, w64, w32));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_damage_q, nblocks(g.ncell), RED_THREADS, 0, s, g, m, u, eig, q, w64, w32));
 }
 
 __global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, const double* eig,
                          RedSlot slot) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
   int NE = elems_per_cell(g.kind);
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < g.ncell;
@@ -379,7 +381,7 @@ __global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, co
 }
 void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* alpha,
             const double* eig, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, k_energy<<<rblocks(g.ncell), RED_THREADS, 0, s>>>(g, m, u, alpha, eig, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_energy, rblocks(g.ncell), RED_THREADS, 0, s, g, m, u, alpha, eig, slot));
 }
 
 // children of coarse element t of coarse cell (I, J): fine cells and fine element types
@@ -389,6 +391,7 @@ void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const 
 //          t2 (top):    TR.2, TR.3, TL.2, TL.1     t3 (left):  TL.3, TL.0, BL.3, BL.2
 template <class T>
 __global__ void k_coarsen(Grid gf, Grid gc, const T* cf, T* cc) {
+  pdl_enter();
   int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= gc.ncell) return;
   int J = cell / gc.nx, I = cell - J * gc.nx;
@@ -408,47 +411,16 @@ __global__ void k_coarsen(Grid gf, Grid gc, const T* cf, T* cc) {
 }
 template <class T>
 void coarsen_coef(cudaStream_t s, const Grid& gf, const Grid& gc, const T* cf, T* cc) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarsen<<<nblocks(gc.ncell), RED_THREADS, 0, s>>>(gf, gc, cf, cc));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_coarsen<T>, nblocks(gc.ncell), RED_THREADS, 0, s, gf, gc, cf, cc));
 }
 template void coarsen_coef<double>(cudaStream_t, const Grid&, const Grid&, const double*, double*);
 template void coarsen_coef<float>(cudaStream_t, const Grid&, const Grid&, const float*, float*);
-
-// element (cell offset, element type, local index) lists around a node
-__device__ __forceinline__ int node_elements(const Grid& g, int node, int* cells, int* ts,
-                                             int* ks) {
-  int cnt = 0;
-  auto push = [&](int ci, int cj, int t, int k) {
-    if (ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny) {
-      cells[cnt] = cj * g.nx + ci;
-      ts[cnt] = t;
-      ks[cnt] = k;
-      ++cnt;
-    }
-  };
-  if (node < g.nv) {
-    int j = node / (g.nx + 1), i = node - j * (g.nx + 1);
-    if (g.kind == CROSSED) {
-      push(i, j, 0, 0); push(i, j, 3, 1);
-      push(i - 1, j, 0, 1); push(i - 1, j, 1, 0);
-      push(i - 1, j - 1, 1, 1); push(i - 1, j - 1, 2, 0);
-      push(i, j - 1, 2, 1); push(i, j - 1, 3, 0);
-    } else {
-      push(i, j, 0, 0); push(i, j, 1, 0);
-      push(i - 1, j, 0, 1);
-      push(i - 1, j - 1, 0, 2); push(i - 1, j - 1, 1, 1);
-      push(i, j - 1, 1, 2);
-    }
-  } else {
-    int c = node - g.nv, j = c / g.nx, i = c - j * g.nx;
-    for (int t = 0; t < 4; ++t) push(i, j, t, 2);
-  }
-  return cnt;
-}
 
 // l1 row sums of the assembled element matrices: D_ii = sum_T sum_j |K_T(i, j)|, so that the
 // spectrum of D^{-1} K lies in (0, 1].
 template <class T>
 __global__ void k_l1_elastic(Grid g, Consts<T> cs, const T* coef, T* dinv) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int cells[8], ts[8], ks[8];
@@ -475,13 +447,14 @@ __global__ void k_l1_elastic(Grid g, Consts<T> cs, const T* coef, T* dinv) {
 }
 template <class T>
 void l1_dinv_elastic(cudaStream_t s, const Grid& g, const Mat& m, const T* coef, T* dinv) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_elastic<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, make_consts<T>(g, m), coef, dinv));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_l1_elastic<T>, nblocks(g.n), RED_THREADS, 0, s, g, make_consts<T>(g, m), coef, dinv));
 }
 template void l1_dinv_elastic<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_elastic<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
 
 template <class T>
 __global__ void k_l1_damage(Grid g, Consts<T> cs, const T* w, T* dinv) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int cells[8], ts[8], ks[8];
@@ -503,7 +476,7 @@ __global__ void k_l1_damage(Grid g, Consts<T> cs, const T* w, T* dinv) {
 }
 template <class T>
 void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* dinv) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_l1_damage<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, make_consts<T>(g, m), w, dinv));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_l1_damage<T>, nblocks(g.n), RED_THREADS, 0, s, g, make_consts<T>(g, m), w, dinv));
 }
 template void l1_dinv_damage<double>(cudaStream_t, const Grid&, const Mat&, const double*, double*);
 template void l1_dinv_damage<float>(cudaStream_t, const Grid&, const Mat&, const float*, float*);
@@ -512,53 +485,17 @@ template void l1_dinv_damage<float>(cudaStream_t, const Grid&, const Mat&, const
 // multigrid transfer (P1 nodal interpolation between nested structured meshes)
 // ---------------------------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ T fget(const Grid& gf, const T* v, bool centre, int i, int j, int c,
-                                  int ncomp) {
-  if (!centre) {
-    if (i < 0 || i > gf.nx || j < 0 || j > gf.ny) return T(0);
-    return v[(j * (gf.nx + 1) + i) * ncomp + c];
-  }
-  if (i < 0 || i >= gf.nx || j < 0 || j >= gf.ny) return T(0);
-  return v[(gf.nv + j * gf.nx + i) * ncomp + c];
-}
-
-template <class T>
 __global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* rf, T* bc,
                            const uint8_t* excl_c) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= gc.n) return;
-  int X2, Y2;
-  node_coords(gc, node, X2, Y2);
-  for (int c = 0; c < ncomp; ++c) {
-    T acc;
-    if ((X2 & 1) == 0) {  // coarse vertex (I, J) = fine vertex (2I, 2J)
-      int i = X2, j = Y2;  // fine vertex indices 2I, 2J
-      acc = fget(gf, rf, false, i, j, c, ncomp);
-      T h = fget(gf, rf, false, i - 1, j, c, ncomp) + fget(gf, rf, false, i + 1, j, c, ncomp) +
-            fget(gf, rf, false, i, j - 1, c, ncomp) + fget(gf, rf, false, i, j + 1, c, ncomp);
-      if (gf.kind == RIGHT) {
-        h += fget(gf, rf, false, i + 1, j + 1, c, ncomp) + fget(gf, rf, false, i - 1, j - 1, c, ncomp);
-      } else {
-        h += fget(gf, rf, true, i, j, c, ncomp) + fget(gf, rf, true, i - 1, j, c, ncomp) +
-             fget(gf, rf, true, i, j - 1, c, ncomp) + fget(gf, rf, true, i - 1, j - 1, c, ncomp);
-      }
-      acc += T(0.5) * h;
-    } else {  // coarse centre (I, J) = fine vertex (2I+1, 2J+1)
-      int I = X2 / 2, J = Y2 / 2;
-      acc = fget(gf, rf, false, 2 * I + 1, 2 * J + 1, c, ncomp);
-      T h = fget(gf, rf, true, 2 * I, 2 * J, c, ncomp) + fget(gf, rf, true, 2 * I + 1, 2 * J, c, ncomp) +
-            fget(gf, rf, true, 2 * I, 2 * J + 1, c, ncomp) +
-            fget(gf, rf, true, 2 * I + 1, 2 * J + 1, c, ncomp);
-      acc += T(0.5) * h;
-    }
-    if (is_fixed(gc, X2, Y2, comp_base + c) || (excl_c && excl_c[node])) acc = T(0);
-    bc[node * ncomp + c] = acc;
-  }
+  restrict_node(gf, gc, ncomp, comp_base, rf, bc, excl_c, node);
 }
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
                   const T* rf, T* bc, const uint8_t* excl_c) {
-  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, rf, bc, excl_c));
+  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, pdl_launch(k_restrict<T>, nblocks(gc.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, rf, bc, excl_c));
 }
 template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
                                    double*, const uint8_t*);
@@ -566,43 +503,17 @@ template void restrict_res<float>(cudaStream_t, const Grid&, const Grid&, int, i
                                   float*, const uint8_t*);
 
 template <class T>
-__device__ __forceinline__ T cget(const Grid& gc, const T* v, bool centre, int I, int J, int c,
-                                  int ncomp) {
-  if (!centre) return v[(J * (gc.nx + 1) + I) * ncomp + c];
-  return v[(gc.nv + J * gc.nx + I) * ncomp + c];
-}
-
-template <class T>
 __global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* xc, T* xf,
                           const uint8_t* excl) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= gf.n) return;
-  int X2, Y2;
-  node_coords(gf, node, X2, Y2);
-  bool ex = excl && excl[node];
-  for (int c = 0; c < ncomp; ++c) {
-    T v;
-    if (node < gf.nv) {
-      int i = X2 / 2, j = Y2 / 2, I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
-      if (!pi && !pj) v = cget(gc, xc, false, I, J, c, ncomp);
-      else if (pi && !pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J, c, ncomp));
-      else if (!pi && pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I, J + 1, c, ncomp));
-      else if (gf.kind == RIGHT)
-        v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J + 1, c, ncomp));
-      else v = cget(gc, xc, true, I, J, c, ncomp);
-    } else {
-      int cc = node - gf.nv, j = cc / gf.nx, i = cc - j * gf.nx;
-      int I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
-      v = T(0.5) * (cget(gc, xc, false, I + pi, J + pj, c, ncomp) + cget(gc, xc, true, I, J, c, ncomp));
-    }
-    if (ex || is_fixed(gf, X2, Y2, comp_base + c)) v = T(0);
-    xf[node * ncomp + c] += v;
-  }
+  prolong_node(gf, gc, ncomp, comp_base, xc, xf, excl, node);
 }
 template <class T>
 void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
                  const T* xc, T* xf, const uint8_t* excl) {
-  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, k_prolong<<<nblocks(gf.n), RED_THREADS, 0, s>>>(gf, gc, ncomp, comp_base, xc, xf, excl));
+  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, pdl_launch(k_prolong<T>, nblocks(gf.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, xc, xf, excl));
 }
 template void prolong_add<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
                                   double*, const uint8_t*);
@@ -615,6 +526,7 @@ template void prolong_add<float>(cudaStream_t, const Grid&, const Grid&, int, in
 template <class T>
 __global__ void k_coarse_assemble(Grid g, Mat m, int physics, const T* coef, T* A, T* diag0,
                                   const uint8_t* excl) {
+  pdl_enter();
   // block = column j, threads = rows i
   const int ncomp = physics == 0 ? 2 : 1;
   const int nd = g.n * ncomp;
@@ -668,7 +580,7 @@ template <class T>
 void coarse_assemble(cudaStream_t s, const Grid& g, const Mat& m, int physics, const T* coef, T* A,
                      T* diag0, const uint8_t* excl) {
   int nd = g.n * (physics == 0 ? 2 : 1);
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_assemble<<<nd, 256, 0, s>>>(g, m, physics, coef, A, diag0, excl));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_coarse_assemble<T>, nd, 256, 0, s, g, m, physics, coef, A, diag0, excl));
 }
 template void coarse_assemble<double>(cudaStream_t, const Grid&, const Mat&, int, const double*,
                                       double*, double*, const uint8_t*);
@@ -679,6 +591,7 @@ template void coarse_assemble<float>(cudaStream_t, const Grid&, const Mat&, int,
 // position is excluded (coarse vertex (I,J) = fine vertex (2I,2J); coarse centre (I,J) = fine
 // vertex (2I+1, 2J+1)).
 __global__ void k_mask_restrict(Grid gf, Grid gc, const uint8_t* ef, uint8_t* ec) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= gc.n) return;
   int X2, Y2;
@@ -687,7 +600,7 @@ __global__ void k_mask_restrict(Grid gf, Grid gc, const uint8_t* ef, uint8_t* ec
 }
 void mask_restrict(cudaStream_t s, const Grid& gf, const Grid& gc, const uint8_t* ef, uint8_t* ec) {
   PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s,
-            k_mask_restrict<<<nblocks(gc.n), RED_THREADS, 0, s>>>(gf, gc, ef, ec));
+            pdl_launch(k_mask_restrict, nblocks(gc.n), RED_THREADS, 0, s, gf, gc, ef, ec));
 }
 
 // In-place Cholesky A = L L^T (lower triangle); a pivot that is not positive relative to the
@@ -695,6 +608,7 @@ void mask_restrict(cudaStream_t s, const Grid& gf, const Grid& gc, const uint8_t
 // preconditioner when the coarse operator is singular).
 template <class T>
 __global__ void k_coarse_factor(int n, T* A, const T* diag0) {
+  pdl_enter();
   __shared__ T piv;
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
@@ -717,7 +631,7 @@ __global__ void k_coarse_factor(int n, T* A, const T* diag0) {
 }
 template <class T>
 void coarse_factor(cudaStream_t s, int n, T* A, const T* diag0) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_factor<<<1, 1024, 0, s>>>(n, A, diag0));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_coarse_factor<T>, 1, 1024, 0, s, n, A, diag0));
 }
 template void coarse_factor<double>(cudaStream_t, int, double*, const double*);
 template void coarse_factor<float>(cudaStream_t, int, float*, const float*);
@@ -725,6 +639,7 @@ template void coarse_factor<float>(cudaStream_t, int, float*, const float*);
 // Column j of A^{-1} from the Cholesky factor (one block per column; set-up time only).
 template <class T>
 __global__ void k_coarse_invert(int n, const T* L, T* Ainv) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);
   const int j = blockIdx.x;
@@ -748,14 +663,141 @@ __global__ void k_coarse_invert(int n, const T* L, T* Ainv) {
 }
 template <class T>
 void coarse_invert(cudaStream_t s, int n, const T* L, T* Ainv) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, k_coarse_invert<<<n, 128, n * sizeof(T), s>>>(n, L, Ainv));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_coarse_invert<T>, n, 128, n * sizeof(T), s, n, L, Ainv));
 }
 template void coarse_invert<double>(cudaStream_t, int, const double*, double*);
 template void coarse_invert<float>(cudaStream_t, int, const float*, float*);
 
+// ---- coarsest level, shared-memory path --------------------------------------------------------
+// The packed lower triangle (row i holds L[i][0..i] at i(i+1)/2) of the coarsest operator fits
+// in one SM's shared memory (n <= 320 in FP32): the factorization runs there with one block,
+// and the inverse with one warp per column against a shared-memory copy of the factor.
+__device__ __forceinline__ int packed(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <class T>
+size_t coarse_smem_bytes(int n) {
+  return (size_t)n * (n + 1) / 2 * sizeof(T) + (size_t)COARSE_WARPS * n * sizeof(T);
+}
+
+// Same pivot rule and the same operations, in the same order per entry, as k_coarse_factor;
+// the packed factor is written back over the first n(n+1)/2 entries of A.
+template <class T>
+__global__ void __launch_bounds__(1024) k_coarse_factor_smem(int n, T* A, const T* diag0) {
+  pdl_enter();
+  extern __shared__ unsigned char smem_raw[];
+  T* L = reinterpret_cast<T*>(smem_raw);
+  T* colk = L + (size_t)n * (n + 1) / 2;  // column k below the diagonal
+  __shared__ T piv;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j <= i; j += 32) L[packed(i, j)] = A[(size_t)i * n + j];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      T d = L[packed(k, k)];
+      T ref = diag0[k] > T(0) ? diag0[k] : T(1);
+      if (!(d > T(1e-10) * ref)) d = ref;
+      piv = sqrt(d);
+      L[packed(k, k)] = piv;
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += nt) {
+      const T v = L[packed(i, k)] / piv;
+      L[packed(i, k)] = v;
+      colk[i] = v;
+    }
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const T lik = colk[i];
+      T* row = L + packed(i, 0);
+      for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * colk[j];
+    }
+    __syncthreads();
+  }
+  const int np = n * (n + 1) / 2;
+  for (int t = tid; t < np; t += nt) A[t] = L[t];
+}
+
+// Column j of A^{-1} = L^{-T} L^{-1} e_j: forward substitution by rows (dot products along row
+// i of L), backward substitution by columns of L^T (row k of L scattered into y).
+template <class T>
+__global__ void __launch_bounds__(32 * COARSE_WARPS) k_coarse_invert_smem(int n, const T* Lp, T* Ainv) {
+  pdl_enter();
+  extern __shared__ unsigned char smem_raw[];
+  T* L = reinterpret_cast<T*>(smem_raw);
+  const int np = n * (n + 1) / 2;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) L[t] = Lp[t];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* y = L + np + (size_t)warp * n;
+  const int j = blockIdx.x * COARSE_WARPS + warp;
+  __syncthreads();
+  if (j >= n) return;
+  for (int i = lane; i < n; i += 32) y[i] = T(0);
+  __syncwarp();
+  for (int i = j; i < n; ++i) {  // forward: L y = e_j (y_i = 0 for i < j)
+    const T* row = L + packed(i, 0);
+    T acc = T(0);
+    for (int k = j + lane; k < i; k += 32) acc += row[k] * y[k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[i] = ((i == j ? T(1) : T(0)) - acc) / row[i];
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {  // backward: L^T x = y, x overwrites y
+    const T* row = L + packed(k, 0);
+    const T xk = y[k] / row[k];
+    __syncwarp();
+    if (lane == 0) y[k] = xk;
+    for (int i = lane; i < k; i += 32) y[i] -= row[i] * xk;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) Ainv[(size_t)j * n + i] = y[i];
+}
+
+// Largest dynamic shared memory both kernels can be given (opt-in limit minus their static
+// shared memory), raised to that once per process and instantiation; 0 if that fails.
+template <class T>
+size_t coarse_smem_limit() {
+  static size_t limit = [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return size_t(0);
+    cudaFuncAttributes fa, fb;
+    if (cudaFuncGetAttributes(&fa, k_coarse_factor_smem<T>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fb, k_coarse_invert_smem<T>) != cudaSuccess)
+      return size_t(0);
+    const size_t st = fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes;
+    if ((size_t)optin <= st) return size_t(0);
+    const int lim = optin - (int)st;
+    if (cudaFuncSetAttribute(k_coarse_factor_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute(k_coarse_invert_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+      return size_t(0);
+    return (size_t)lim;
+  }();
+  return limit;
+}
+
+template <class T>
+void coarse_factor_invert(cudaStream_t s, int n, T* A, const T* diag0, T* Ainv) {
+  const size_t smem = coarse_smem_bytes<T>(n);
+  if (smem > coarse_smem_limit<T>()) {  // does not fit (FP64 elastic): global-memory kernels
+    coarse_factor<T>(s, n, A, diag0);
+    coarse_invert<T>(s, n, A, Ainv);
+    return;
+  }
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s,
+            pdl_launch(k_coarse_factor_smem<T>, 1, 1024, smem, s, n, A, diag0));
+  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s,
+            pdl_launch(k_coarse_invert_smem<T>, (n + COARSE_WARPS - 1) / COARSE_WARPS,
+                       32 * COARSE_WARPS, smem, s, n, (const T*)A, Ainv));
+}
+template void coarse_factor_invert<double>(cudaStream_t, int, double*, const double*, double*);
+template void coarse_factor_invert<float>(cudaStream_t, int, float*, const float*, float*);
+
 // x = A^{-1} b with the stored symmetric inverse: thread i reads column i (coalesced).
 template <class T>
 __global__ void k_coarse_solve(int n, const T* Ainv, const T* b, T* x) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* bs = reinterpret_cast<T*>(smem_raw);
   for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = b[i];
@@ -769,7 +811,7 @@ __global__ void k_coarse_solve(int n, const T* Ainv, const T* b, T* x) {
 template <class T>
 void coarse_solve(cudaStream_t s, int n, const T* Ainv, const T* b, T* x) {
   int threads = n < 1024 ? ((n + 31) / 32) * 32 : 1024;
-  PF_LAUNCH(kclass(KC_COARSE, false, false), 0.0, s, k_coarse_solve<<<1, threads, n * sizeof(T), s>>>(n, Ainv, b, x));
+  PF_LAUNCH(kclass(KC_COARSE, false, false), 0.0, s, pdl_launch(k_coarse_solve<T>, 1, threads, n * sizeof(T), s, n, Ainv, b, x));
 }
 template void coarse_solve<double>(cudaStream_t, int, const double*, const double*, double*);
 template void coarse_solve<float>(cudaStream_t, int, const float*, const float*, float*);
@@ -777,6 +819,7 @@ template void coarse_solve<float>(cudaStream_t, int, const float*, const float*,
 // Active components are within the zero tolerance of their bound (eq. reducedis): the step puts
 // them on it, d_i = bound_i - x_i; inactive components keep the reduced Newton step.
 __global__ void k_snap_active(Grid g, const uint8_t* act, const double* x, const double* lo, double* d) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const uint8_t a = act[i];
@@ -786,7 +829,7 @@ __global__ void k_snap_active(Grid g, const uint8_t* act, const double* x, const
 void snap_active(cudaStream_t s, const Grid& g, const uint8_t* act, const double* x, const double* lo,
                  double* d) {
   PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s,
-            k_snap_active<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, act, x, lo, d));
+            pdl_launch(k_snap_active, nblocks(g.n), RED_THREADS, 0, s, g, act, x, lo, d));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -805,6 +848,7 @@ __device__ __forceinline__ void dphi(double a, double b, double& da, double& db)
 }
 __global__ void k_merit_parts(Grid g, const double* x, const double* F, const double* lo, double* v,
                               double* dg) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   double l = lo[i], h = upper_of(g, i, l);
@@ -819,14 +863,15 @@ __global__ void k_merit_parts(Grid g, const double* x, const double* F, const do
 }
 void merit_parts(cudaStream_t s, const Grid& g, const double* x, const double* F,
                  const double* lo, double* v, double* dg) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_merit_parts<<<nblocks(g.n), RED_THREADS, 0, s>>>(g, x, F, lo, v, dg));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_merit_parts, nblocks(g.n), RED_THREADS, 0, s, g, x, F, lo, v, dg));
 }
 __global__ void k_merit_dir(size_t n, const double* dg, const double* Hv, double* d) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) d[i] = -(dg[i] + Hv[i]);
 }
 void merit_direction(cudaStream_t s, size_t n, const double* dg, const double* Hv, double* d) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, k_merit_dir<<<nblocks(n), RED_THREADS, 0, s>>>(n, dg, Hv, d));
+  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_merit_dir, nblocks(n), RED_THREADS, 0, s, n, dg, Hv, d));
 }
 
 }  // namespace pf

@@ -63,6 +63,7 @@ pf_status scratch_address(double** out) {
 // beta T at element centroids per (cell row, element type), T = -dT erfc(y / pen)
 __global__ void k_eig_rows(double* eig, int ny, int kind, double hy, double beta, double dT,
                            double pen) {
+  pdl_enter();
   int NE = elems_per_cell(kind);
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ny * NE) return;

@@ -23,7 +23,7 @@ template <class Op>
 static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
   dim3 block(TX, TY);
   dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
-  PF_LAUNCH(id, bytes, s, stencil_kernel<Op><<<grid, block, 0, s>>>(op));
+  PF_LAUNCH(id, bytes, s, pdl_launch(stencil_kernel<Op>, grid, block, 0, s, op));
 }
 
 template <class T, int K, int C, int M, bool E, bool D>

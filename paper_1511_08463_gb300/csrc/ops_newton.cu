@@ -8,7 +8,7 @@ template <class Op>
 static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
   dim3 block(TX, TY);
   dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
-  PF_LAUNCH(id, bytes, s, stencil_kernel<Op><<<grid, block, 0, s>>>(op));
+  PF_LAUNCH(id, bytes, s, pdl_launch(stencil_kernel<Op>, grid, block, 0, s, op));
 }
 
 template <class T, int K, bool TR>
@@ -39,6 +39,7 @@ template void launch_coupling<float>(cudaStream_t, const Grid&, const Mat&, bool
 // z = a x + b y + c z (c == 0: z not read); scalars from the host
 template <class T>
 __global__ void k_lincomb(T* z, T a, const T* x, T b, const T* y, T c, size_t n) {
+  pdl_enter();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   T v = a * x[i];
@@ -50,7 +51,7 @@ template <class T>
 void vec_lincomb(cudaStream_t s, T* z, T a, const T* x, T b, const T* y, T c, size_t n) {
   if (n == 0) return;
   PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, false), 3.0 * n * sizeof(T), s,
-            k_lincomb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, a, x, b, y, c, n));
+            pdl_launch(k_lincomb<T>, (unsigned)((n + 255) / 256), 256, 0, s, z, a, x, b, y, c, n));
 }
 template void vec_lincomb<double>(cudaStream_t, double*, double, const double*, double,
                                   const double*, double, size_t);
@@ -61,6 +62,7 @@ template void vec_lincomb<float>(cudaStream_t, float*, float, const float*, floa
 __global__ void k_newton_trial(Grid g, double* u, const double* u0, const double* du, double* alpha,
                                const double* a0, const double* da, const double* lo, float* a32,
                                double mu) {
+  pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.n) return;
   int X2, Y2;
@@ -77,7 +79,7 @@ void newton_trial(cudaStream_t s, const Grid& g, double* u, const double* u0, co
                   double* alpha, const double* a0, const double* da, const double* lo, float* a32,
                   double mu) {
   PF_LAUNCH(kclass(KC_VECTOR, true, false), 0.0, s,
-            k_newton_trial<<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(g, u, u0, du, alpha, a0, da,
+            pdl_launch(k_newton_trial, (unsigned)((g.n + 255) / 256), 256, 0, s, g, u, u0, du, alpha, a0, da,
                                                                          lo, a32, mu));
 }
 

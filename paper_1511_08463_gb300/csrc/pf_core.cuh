@@ -16,6 +16,36 @@
 
 namespace pf {
 
+// Programmatic dependent launch (PDL).  Every kernel of the library starts with pdl_enter():
+// griddepcontrol.wait blocks until the kernel launched before it on the stream has completed
+// and its memory is visible, and launch_dependents then lets the next kernel be launched and
+// scheduled while this one runs.  Each kernel thus still sees all effects of its predecessor
+// (stream order is kept), but the next launch's latency overlaps this kernel's execution --
+// which matters for the many small kernels of the coarse multigrid levels.  Both instructions
+// are no-ops for a kernel launched without the PDL attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `k` on `s` with the programmatic-stream-serialization attribute (errors are reported
+// by cudaGetLastError, like a triple-chevron launch).
+template <class... KArgs, class... Args>
+inline void pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 constexpr int RIGHT = 0;
 constexpr int CROSSED = 1;
 constexpr int TX = 32;  // stencil tile: vertices per block in x

@@ -105,6 +105,14 @@ void prof_post(int id, double bytes, cudaStream_t s) {
   }
 }
 
+namespace {
+thread_local std::string t_failed_launch;
+}
+void prof_note_launch(const char* expr) {
+  if (t_failed_launch.empty() && cudaPeekAtLastError() != cudaSuccess) t_failed_launch = expr;
+}
+const char* prof_failed_launch() { return t_failed_launch.c_str(); }
+
 void prof_add_launches(int64_t n) { g.launches.fetch_add(n, std::memory_order_relaxed); }
 void prof_set_capturing(bool on) {
   t_capturing = on;

@@ -34,6 +34,9 @@ int64_t prof_captured();
 int64_t prof_launches();
 void prof_post(int id, double bytes, cudaStream_t s);
 const char* kclass_name(int id);
+// a launch that failed records its expression (this thread; read by the error reporting)
+void prof_note_launch(const char* expr);
+const char* prof_failed_launch();
 
 }  // namespace pf
 
@@ -41,5 +44,6 @@ const char* kclass_name(int id);
   do {                                         \
     ::pf::prof_pre((ID), (STREAM));            \
     __VA_ARGS__;                               \
+    ::pf::prof_note_launch(#__VA_ARGS__);      \
     ::pf::prof_post((ID), (BYTES), (STREAM));  \
   } while (0)

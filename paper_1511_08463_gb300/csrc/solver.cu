@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
+#include <type_traits>
 #include <new>
 #include <string>
 
@@ -40,8 +41,9 @@ static bool debug_enabled() {
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
     if (e_ != cudaSuccess)                                                             \
-      return fail(PF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
-                  __FILE__, __LINE__);                                                 \
+      return fail(PF_ECUDA, "%s failed: %s (%s:%d)%s%.160s", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__, *prof_failed_launch() ? "; first failed launch: " : "", \
+                  prof_failed_launch());                                               \
   } while (0)
 #define TRY(expr)                    \
   do {                               \
@@ -438,8 +440,85 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
   if (cx != x) cudaMemcpyAsync(x, cx, nd * sizeof(T), cudaMemcpyDeviceToDevice, st);
 }
 
+// Level from which the rest of an FP32 V-cycle runs in the single-block kernel (tail.cu),
+// provided the hierarchy ends in a dense solve, all levels are in use and the tail spans at
+// least two levels: level 0 if the whole hierarchy fits in one block's shared memory (the
+// V-cycle becomes one launch), else the first level of at most TAIL_MAX_NODES nodes (a larger
+// level keeps one SM busy for longer than its grid-wide launches take).  -1: no tail.
+// shared-memory floats of one tail level: x, x_new, b, d, dinv (nc per node), coefficients per
+// element, then one flag byte per node (+ one exclusion byte per node for the damage operator)
+size_t tail_level_floats(const Grid& g, int nc) {
+  return 5 * (size_t)nc * g.n + g.nelem + ((size_t)(nc == 1 ? 2 : 1) * g.n + 3) / 4;
+}
+
+int tail_first(pf_sim& s, int phys) {
+  const int nlev = (int)s.lv.size();
+  if (!s.use_tail || s.nl_active != nlev || nlev < 2 || !s.lv[nlev - 1].dense) return -1;
+  if (s.tail_first[phys] != -2) return s.tail_first[phys];
+  const size_t limit = tail_smem_limit();
+  const int nc = phys == ELASTIC ? 2 : 1;
+  const int nrc = phys == ELASTIC ? 3 : 4;  // element record components
+  int best = -1;
+  size_t acc = 0;
+  int small = -1;  // first level of at most TAIL_MAX_NODES nodes that fits
+  for (int l = nlev - 1; l >= 0 && nlev - l <= MAX_TAIL; --l) {
+    const Grid& g = s.lv[l].g;
+    acc += tail_level_floats(g, nc) * sizeof(float);
+    // records of the largest (this) level
+    if (acc + (size_t)nrc * g.nelem * sizeof(float) > limit) break;
+    best = l;
+    if (g.n <= TAIL_MAX_NODES) small = l;
+  }
+  if (best != 0) best = small;
+  if (best > nlev - 2) best = -1;
+  s.tail_first[phys] = best;
+  return best;
+}
+
+void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x, int deg) {
+  const int nlev = (int)s.lv.size(), l0 = s.tail_first[phys];
+  const int nc = phys == ELASTIC ? 2 : 1;
+  TailArgs a{};
+  a.nl = nlev - l0;
+  a.deg = deg;
+  a.dense = 1;
+  a.coarse_steps = 8 * deg;
+  const Level& Lc = s.lv[nlev - 1];
+  a.Ainv = phys == ELASTIC ? Lc.f32.AEi : Lc.f32.ADi;
+  a.b_in = b;
+  a.x_out = x;
+  int off = 0;
+  for (int k = 0; k < a.nl; ++k) {
+    const Level& L = s.lv[l0 + k];
+    TailLevel& t = a.L[k];
+    t.g = L.g;
+    t.cs = make_consts<float>(L.g, s.m);
+    t.coef = phys == ELASTIC ? L.f32.coefE : L.f32.wD;
+    t.dinv = phys == ELASTIC ? L.f32.dinvE : L.f32.dinvD;
+    t.excl = phys == DAMAGE ? (l0 + k == 0 ? s.act : L.exclD) : nullptr;
+    const int nd = nc * L.g.n;
+    t.ox = off;
+    t.oxn = t.ox + nd;
+    t.ob = t.oxn + nd;
+    t.od = t.ob + nd;
+    t.odi = t.od + nd;
+    t.oc = t.odi + nd;
+    t.oe = t.oc + L.g.nelem;
+    off += (int)tail_level_floats(L.g, nc);
+  }
+  a.orec = off;  // records of the largest level (the first)
+  off += (phys == ELASTIC ? 3 : 4) * s.lv[l0].g.nelem;
+  tail_vcycle(st, nc, a, (size_t)off * sizeof(float));
+}
+
 template <class T>
 void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int deg) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (l == tail_first(s, phys)) {
+      launch_tail(s, st, phys, b, x, deg);
+      return;
+    }
+  }
   Level& L = s.lv[l];
   LevelBuf<T>& B = L.buf<T>();
   const int nc = phys == ELASTIC ? 2 : 1;
@@ -489,8 +568,7 @@ void setup_elastic(pf_sim& s, cudaStream_t st) {
   if (Lc.dense && nlev > 1) {
     LevelBuf<T>& B = Lc.buf<T>();
     coarse_assemble<T>(st, Lc.g, s.m, ELASTIC, B.coefE, B.AE, B.diagE, nullptr);
-    coarse_factor<T>(st, 2 * Lc.g.n, B.AE, B.diagE);
-    coarse_invert<T>(st, 2 * Lc.g.n, B.AE, B.AEi);
+    coarse_factor_invert<T>(st, 2 * Lc.g.n, B.AE, B.diagE, B.AEi);
   }
 }
 
@@ -514,8 +592,7 @@ void damage_masks(pf_sim& s, cudaStream_t st) {
   if (Lc.dense && nlev > 1) {
     LevelBuf<T>& B = Lc.buf<T>();
     coarse_assemble<T>(st, Lc.g, s.m, DAMAGE, B.wD, B.AD, B.diagD, Lc.exclD);
-    coarse_factor<T>(st, Lc.g.n, B.AD, B.diagD);
-    coarse_invert<T>(st, Lc.g.n, B.AD, B.ADi);
+    coarse_factor_invert<T>(st, Lc.g.n, B.AD, B.diagD, B.ADi);
   }
 }
 
@@ -566,7 +643,8 @@ pf_status pcg_host(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, 
 template <class T>
 pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   const int pi = sizeof(T) == 8 ? 1 : 0;
-  if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == deg && s.cg_nl[phys][pi] == s.nl_active)
+  if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == deg && s.cg_nl[phys][pi] == s.nl_active &&
+      s.cg_tail[phys][pi] == (int)s.use_tail)
     return PF_OK;
   if (s.cg_exec[phys][pi]) {
     cudaGraphExecDestroy(s.cg_exec[phys][pi]);
@@ -618,6 +696,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   s.cg_body_kernels[phys][pi] = (int)nk;
   s.cg_deg[phys][pi] = deg;
   s.cg_nl[phys][pi] = s.nl_active;
+  s.cg_tail[phys][pi] = (int)s.use_tail;
   return PF_OK;
 }
 
@@ -1368,6 +1447,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->batch_workers = 8;
   o->am_forcing = 0.0;
   o->am_forcing_max = 1e-3;
+  o->mg_tail = 1;
   return PF_OK;
 }
 
@@ -1476,6 +1556,7 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
+  s->use_tail = o->mg_tail != 0;
   pf_step_report r{};
   r.omega_bar_min = o->omega;
   pf_status status = begin_step(*s, st, *L);
@@ -1650,6 +1731,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
+  s->use_tail = o->mg_tail != 0;
   s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   pf_step_report r{};
   pf_status status = u_solve(*s, st, *o, &r);
@@ -1671,6 +1753,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
+  s->use_tail = o->mg_tail != 0;
   pf_step_report r{};
   pf_status status = alpha_solve(*s, st, *o, &r);
   if (status == PF_OK || status == PF_ENOTCONV) {

@@ -129,6 +129,11 @@ struct pf_sim {
   int cg_nl[2][2] = {};
   // multigrid levels used by the solves (pf_solver_opts.mg_levels_max; all by default)
   int nl_active = 1;
+  // single-block tail of the FP32 V-cycle (pf_solver_opts.mg_tail): first level per operator
+  // (-1: none; -2: not computed yet) and its shared-memory bytes
+  bool use_tail = true;
+  int tail_first[2] = {-2, -2};
+  int cg_tail[2][2] = {};
   double* host = nullptr;  // pinned read-back slot from the context's pool
   ~pf_sim() {
     if (host && ctx) ctx->give_slot(host);

@@ -45,6 +45,7 @@ inline Consts<T> make_consts(const Grid& g, const Mat& m) {
 // ----------------------------------------------------------------------------------------------
 template <class Op>
 __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
+  pdl_enter();
   using V = typename Op::V;
   using R = typename Op::R;
   using ET = typename Op::ET;

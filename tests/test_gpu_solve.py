@@ -157,3 +157,25 @@ def test_graph_and_host_loops_agree_bitwise():
         np.testing.assert_array_equal(a, b)
     for ra, rb in zip(out[0][1], out[1][1]):
         assert ra["cg_iters_u"] == rb["cg_iters_u"] and ra["cg_iters_alpha"] == rb["cg_iters_alpha"]
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_single_block_tail_matches_grid_vcycle(n):
+    """The coarse levels run as one thread block (mg_tail=1) or one grid per step (mg_tail=0):
+    the same V-cycle up to summation order, so the same solutions and iteration counts."""
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    w = W.notched_square(n=n, n_steps=10, t_max=1.0)
+    out = []
+    for tail in (1, 0):
+        g = S.Sim(w)
+        opts = tight_opts(S, omega=1.5, precision="mixed", mg_tail=tail)
+        reps = [g.load_step(t, dT, opts) for (t, dT) in w.loads[:5]]
+        out.append((g.get_fields(), reps))
+    (u1, a1, _), r1 = out[0]
+    (u0, a0, _), r0 = out[1]
+    assert rel_max(u1, u0) <= 1e-8 and np.abs(a1 - a0).max() <= 1e-8
+    for x, y in zip(r1, r0):
+        np.testing.assert_allclose(x["energy"], y["energy"], rtol=1e-10, atol=1e-15)
+        assert abs(x["cg_iters_u"] - y["cg_iters_u"]) <= max(2, 0.05 * y["cg_iters_u"])
