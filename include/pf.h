@@ -139,6 +139,8 @@ typedef struct pf_solver_opts {
   int32_t mg_tail;         /* 1 (default): in FP32 V-cycles, the coarse levels that fit in one
                             * SM's shared memory run as a single thread block; 0: one grid per
                             * step on every level */
+  int32_t mg_coarse_degree; /* Chebyshev steps per smoothing on the coarse levels (0 (default):
+                             * mg_degree) */
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step). */

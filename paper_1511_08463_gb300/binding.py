@@ -50,7 +50,8 @@ class pf_solver_opts(C.Structure):
                 ("newton_maxit", C.c_int32), ("minres_maxit", C.c_int32),
                 ("minres_rtol", C.c_double), ("use_graphs", C.c_int32),
                 ("batch_workers", C.c_int32), ("am_forcing", C.c_double),
-                ("am_forcing_max", C.c_double), ("mg_tail", C.c_int32)]
+                ("am_forcing_max", C.c_double), ("mg_tail", C.c_int32),
+                ("mg_coarse_degree", C.c_int32)]
 
 
 class pf_step_report(C.Structure):

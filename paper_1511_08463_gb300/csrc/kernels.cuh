@@ -77,13 +77,14 @@ void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* 
 // ---- multigrid transfer -------------------------------------------------------------------------
 // bc = P^T rf on the coarse grid (comp_base: 0 elastic (2 comps), 2 damage (1 comp)); coarse
 // prescribed components set to 0.
+// level: index of the fine level (launch accounting)
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                  const T* rf, T* bc, const uint8_t* excl_c);  // excl_c (may be null): zeroed
+                  const T* rf, T* bc, const uint8_t* excl_c, int level);  // excl_c may be null
 // xf += P xc on free components; excl (fine, may be null) zeroes excluded nodes
 template <class T>
 void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                 const T* xc, T* xf, const uint8_t* excl);
+                 const T* xc, T* xf, const uint8_t* excl, int level);
 
 // ---- coarsest level dense solve -----------------------------------------------------------------
 template <class T>
@@ -109,6 +110,8 @@ struct TailLevel {
 };
 struct TailArgs {
   int nl, deg, dense, coarse_steps;  // levels in the tail; smoothing steps; dense coarsest?
+  int deg0;                          // smoothing steps on the tail's first level
+  int first_level;                   // hierarchy index of that level (launch accounting)
   int orec;                          // shared-memory offset of the element records, in floats
   const float* Ainv;                 // coarsest inverse (dense)
   const float* b_in;                 // right-hand side on the tail's first level (device)

@@ -28,7 +28,7 @@ __global__ void k_fill(T* y, T v, size_t n) {
 }
 template <class T>
 void vec_fill(cudaStream_t s, T* y, T v, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_fill<T>, nblocks(n), RED_THREADS, 0, s, y, v, n));
+  PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, 0), double(n) * sizeof(T), s, pdl_launch(k_fill<T>, nblocks(n), RED_THREADS, 0, s, y, v, n));
 }
 template void vec_fill<double>(cudaStream_t, double*, double, size_t);
 template void vec_fill<float>(cudaStream_t, float*, float, size_t);
@@ -41,7 +41,7 @@ __global__ void k_convert(TO* y, const TI* x, size_t n) {
 }
 template <class TO, class TI>
 void vec_convert(cudaStream_t s, TO* y, const TI* x, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_convert<TO, TI>, nblocks(n), RED_THREADS, 0, s, y, x, n));
+  PF_LAUNCH(kclass(KC_VECTOR, false, 0), double(n) * (sizeof(TO) + sizeof(TI)), s, pdl_launch(k_convert<TO, TI>, nblocks(n), RED_THREADS, 0, s, y, x, n));
 }
 template void vec_convert<float, double>(cudaStream_t, float*, const double*, size_t);
 template void vec_convert<double, float>(cudaStream_t, double*, const float*, size_t);
@@ -53,7 +53,7 @@ __global__ void k_add_f32_to_f64(double* x, const float* d, size_t n) {
   if (i < n) x[i] += (double)d[i];
 }
 void vec_add_f32_to_f64(cudaStream_t s, double* x, const float* d, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_add_f32_to_f64, nblocks(n), RED_THREADS, 0, s, x, d, n));
+  PF_LAUNCH(kclass(KC_VECTOR, true, 0), double(n) * 20.0, s, pdl_launch(k_add_f32_to_f64, nblocks(n), RED_THREADS, 0, s, x, d, n));
 }
 
 template <class T>
@@ -64,7 +64,7 @@ __global__ void k_add(T* x, const T* d, size_t n) {
 }
 template <class T>
 void vec_add(cudaStream_t s, T* x, const T* d, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_add<T>, nblocks(n), RED_THREADS, 0, s, x, d, n));
+  PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, 0), 3.0 * n * sizeof(T), s, pdl_launch(k_add<T>, nblocks(n), RED_THREADS, 0, s, x, d, n));
 }
 template void vec_add<double>(cudaStream_t, double*, const double*, size_t);
 template void vec_add<float>(cudaStream_t, float*, const float*, size_t);
@@ -77,7 +77,7 @@ __global__ void k_mul(T* z, const T* a, const T* b, size_t n) {
 }
 template <class T>
 void vec_mul(cudaStream_t s, T* z, const T* a, const T* b, size_t n) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_mul<T>, nblocks(n), RED_THREADS, 0, s, z, a, b, n));
+  PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, 0), 3.0 * n * sizeof(T), s, pdl_launch(k_mul<T>, nblocks(n), RED_THREADS, 0, s, z, a, b, n));
 }
 template void vec_mul<double>(cudaStream_t, double*, const double*, const double*, size_t);
 template void vec_mul<float>(cudaStream_t, float*, const float*, const float*, size_t);
@@ -93,7 +93,7 @@ __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
 }
 template <class T>
 void vec_dot(cudaStream_t s, const T* x, const T* y, size_t n, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_dot<T>, rblocks(n), RED_THREADS, 0, s, x, y, n, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, sizeof(T) == 8, 0), 2.0 * n * sizeof(T), s, pdl_launch(k_dot<T>, rblocks(n), RED_THREADS, 0, s, x, y, n, slot));
 }
 template void vec_dot<double>(cudaStream_t, const double*, const double*, size_t, RedSlot);
 template void vec_dot<float>(cudaStream_t, const float*, const float*, size_t, RedSlot);
@@ -119,7 +119,7 @@ __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const dou
 template <class T>
 void cg_update_xr(cudaStream_t s, T* x, T* r, const T* p, const T* Ap, size_t n, const double* rz,
                   const double* pAp, RedSlot slot) {
-  PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_cg_xr<T>, rblocks(n), RED_THREADS, 0, s, x, r, p, Ap, n, rz, pAp, slot));
+  PF_LAUNCH(kclass(KC_REDUCE, sizeof(T) == 8, 0), 6.0 * n * sizeof(T), s, pdl_launch(k_cg_xr<T>, rblocks(n), RED_THREADS, 0, s, x, r, p, Ap, n, rz, pAp, slot));
 }
 template void cg_update_xr<double>(cudaStream_t, double*, double*, const double*, const double*,
                                    size_t, const double*, const double*, RedSlot);
@@ -141,7 +141,7 @@ __global__ void k_cg_p(T* p, const T* z, size_t n, const double* rz_new, const d
 template <class T>
 void cg_update_p(cudaStream_t s, T* p, const T* z, size_t n, const double* rz_new,
                  const double* rz_old) {
-  PF_LAUNCH(kclass(KC_VECTOR, false, false), 0.0, s, pdl_launch(k_cg_p<T>, nblocks(n), RED_THREADS, 0, s, p, z, n, rz_new, rz_old));
+  PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, 0), 3.0 * n * sizeof(T), s, pdl_launch(k_cg_p<T>, nblocks(n), RED_THREADS, 0, s, p, z, n, rz_new, rz_old));
 }
 template void cg_update_p<double>(cudaStream_t, double*, const double*, size_t, const double*,
                                   const double*);
@@ -494,13 +494,16 @@ __global__ void k_restrict(Grid gf, Grid gc, int ncomp, int comp_base, const T* 
 }
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                  const T* rf, T* bc, const uint8_t* excl_c) {
-  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, pdl_launch(k_restrict<T>, nblocks(gc.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, rf, bc, excl_c));
+                  const T* rf, T* bc, const uint8_t* excl_c, int level) {
+  // read the fine residual, write the coarse right-hand side (+ coarse mask bytes)
+  const double bytes = double(ncomp) * sizeof(T) * (gf.n + gc.n) + (excl_c ? double(gc.n) : 0.0);
+  PF_LAUNCH(kclass(KC_TRANSFER, sizeof(T) == 8, level), bytes, s,
+            pdl_launch(k_restrict<T>, nblocks(gc.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, rf, bc, excl_c));
 }
 template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
-                                   double*, const uint8_t*);
+                                   double*, const uint8_t*, int);
 template void restrict_res<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
-                                  float*, const uint8_t*);
+                                  float*, const uint8_t*, int);
 
 template <class T>
 __global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* xc, T* xf,
@@ -512,13 +515,16 @@ __global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* x
 }
 template <class T>
 void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                 const T* xc, T* xf, const uint8_t* excl) {
-  PF_LAUNCH(kclass(KC_TRANSFER, false, false), 0.0, s, pdl_launch(k_prolong<T>, nblocks(gf.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, xc, xf, excl));
+                 const T* xc, T* xf, const uint8_t* excl, int level) {
+  // read the coarse correction, read and write the fine iterate (+ fine mask bytes)
+  const double bytes = double(ncomp) * sizeof(T) * (gc.n + 2.0 * gf.n) + (excl ? double(gf.n) : 0.0);
+  PF_LAUNCH(kclass(KC_TRANSFER, sizeof(T) == 8, level), bytes, s,
+            pdl_launch(k_prolong<T>, nblocks(gf.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, xc, xf, excl));
 }
 template void prolong_add<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
-                                  double*, const uint8_t*);
+                                  double*, const uint8_t*, int);
 template void prolong_add<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
-                                 float*, const uint8_t*);
+                                 float*, const uint8_t*, int);
 
 // ---------------------------------------------------------------------------------------------
 // coarsest level: dense assembly, Cholesky and triangular solves in one thread block

@@ -13,7 +13,7 @@ static double elastic_bytes(const Grid& g, int coef, int mode, const ElasticArgs
     case M_MASKED: node = 4 * t; break;
     case M_RESB: node = 6 * t; break;
     case M_RESID: node = 4 * t; break;
-    case M_CHEB: node = (a.d ? 12 : 10) * t; break;
+    case M_CHEB: node = ((a.x ? 2 : 0) + (a.d ? 2 : 0) + 8) * t; break;  // b, dinv, y, d' (+ x, d)
   }
   double coefb = coef == COEF_ALPHA ? double(g.n) * t : double(g.nelem) * t;
   return double(g.n) * node + coefb;
@@ -35,7 +35,7 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>
   op.args = a;
   const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
                  : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;
-  launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse != 0), elastic_bytes<T>(g, C, M, a));
+  launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse), elastic_bytes<T>(g, C, M, a));
 }
 
 template <class T, int K>

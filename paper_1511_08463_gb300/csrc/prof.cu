@@ -67,7 +67,7 @@ void harvest() {
 const char* BASE_NAMES[KC_BASE_COUNT] = {
     "elastic_apply", "elastic_masked", "elastic_resb", "elastic_resid", "elastic_cheb",
     "damage_apply", "damage_masked", "damage_resb", "damage_cheb", "damage_grad", "damage_trial",
-    "vector", "reduce", "transfer", "setup", "coarse_solve"};
+    "vector", "reduce", "transfer", "setup", "coarse_solve", "tail_vcycle"};
 
 }  // namespace
 
@@ -124,10 +124,10 @@ int64_t prof_launches() { return g.launches.load(); }
 const char* kclass_name(int id) {
   static thread_local std::string s;
   if (id < 0 || id >= KC_COUNT) return "";
-  int base = id % KC_BASE_COUNT, var = id / KC_BASE_COUNT;
+  const int base = id % KC_BASE_COUNT, var = id / KC_BASE_COUNT;
   s = BASE_NAMES[base];
-  s += (var & 2) ? "_f64" : "_f32";
-  s += (var & 1) ? "_coarse" : "_l0";
+  s += var >= KC_LEVELS ? "_f64_l" : "_f32_l";
+  s += std::to_string(var % KC_LEVELS);
   return s.c_str();
 }
 

@@ -16,13 +16,16 @@ namespace pf {
 enum KernelClass : int {
   KC_EL_APPLY = 0, KC_EL_MASKED, KC_EL_RESB, KC_EL_RESID, KC_EL_CHEB,
   KC_DM_APPLY, KC_DM_MASKED, KC_DM_RESB, KC_DM_CHEB, KC_DM_GRAD, KC_DM_TRIAL,
-  KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_BASE_COUNT
+  KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_TAIL, KC_BASE_COUNT
 };
-// class id = base + KC_BASE_COUNT * variant, variant = (fp64 ? 2 : 0) + (coarse level ? 1 : 0)
-constexpr int KC_COUNT = KC_BASE_COUNT * 4;
+// class id = base + KC_BASE_COUNT * (precision * KC_LEVELS + multigrid level), so that one class
+// is one kernel at one problem size (deeper levels than KC_LEVELS - 1 share the last class)
+constexpr int KC_LEVELS = 10;
+constexpr int KC_COUNT = KC_BASE_COUNT * 2 * KC_LEVELS;
 
-inline int kclass(int base, bool fp64, bool coarse) {
-  return base + KC_BASE_COUNT * ((fp64 ? 2 : 0) + (coarse ? 1 : 0));
+inline int kclass(int base, bool fp64, int level) {
+  level = level < 0 ? 0 : (level >= KC_LEVELS ? KC_LEVELS - 1 : level);
+  return base + KC_BASE_COUNT * ((fp64 ? KC_LEVELS : 0) + level);
 }
 
 void prof_pre(int id, cudaStream_t s);

@@ -321,6 +321,10 @@ template <>
 Krylov<float>& kry<float>(pf_sim& s) { return s.k32; }
 
 // y = A x on level l (masked operator of the free/inactive set), optional fused x.y
+// The multigrid and Krylov operators read the per-element coefficient abar_T stored by the
+// set-up on every level, level 0 included (the stencil is issue-bound, and recomputing abar_T
+// from the nodal damage in every element of every sweep costs more instructions than the
+// coefficient's bytes); the FP64 physical residual computes abar_T from alpha itself.
 template <class T>
 void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, bool dot, int sl) {
   Level& L = s.lv[l];
@@ -331,8 +335,8 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
     a.coef = L.buf<T>().coefE;
     a.y = y;
     a.slot = slot(s, sl);
-    a.coarse = l > 0;
-    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_MASKED, false, dot, a);
+    a.coarse = l;
+    launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_MASKED, false, dot, a);
   } else {
     DamageArgs<T> a{};
     a.x = x;
@@ -340,7 +344,7 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
     a.excl = l == 0 ? s.act : L.exclD;
     a.y = y;
     a.slot = slot(s, sl);
-    a.coarse = l > 0;
+    a.coarse = l;
     launch_damage<T>(st, L.g, s.m, M_MASKED, dot, a);
   }
 }
@@ -355,8 +359,8 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     a.coef = L.buf<T>().coefE;
     a.b = b;
     a.y = r;
-    a.coarse = l > 0;
-    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_RESB, false, false, a);
+    a.coarse = l;
+    launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_RESB, false, false, a);
   } else {
     DamageArgs<T> a{};
     a.x = x;
@@ -364,7 +368,7 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     a.excl = l == 0 ? s.act : L.exclD;
     a.b = b;
     a.y = r;
-    a.coarse = l > 0;
+    a.coarse = l;
     launch_damage<T>(st, L.g, s.m, M_RESB, false, a);
   }
 }
@@ -385,8 +389,8 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.cr = T(cr);
     a.y = xo;
     a.dout = dout;
-    a.coarse = l > 0;
-    launch_elastic<T>(st, L.g, s.m, l == 0 ? COEF_ALPHA : COEF_ELEM, M_CHEB, false, false, a);
+    a.coarse = l;
+    launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_CHEB, false, false, a);
   } else {
     DamageArgs<T> a{};
     a.x = x;
@@ -399,7 +403,7 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.cr = T(cr);
     a.y = xo;
     a.dout = dout;
-    a.coarse = l > 0;
+    a.coarse = l;
     launch_damage<T>(st, L.g, s.m, M_CHEB, false, a);
   }
 }
@@ -415,8 +419,11 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
   const double lmax = 1.0, lmin = 0.1;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
-  if (from_zero) vec_fill<T>(st, x, T(0), nd);
-  T *cx = x, *nx_ = B.xt, *cd_ = nullptr, *nd_ = B.d;
+  // From zero the first step reads no x (the kernel takes x = 0), so no fill is needed, and the
+  // first output buffer is chosen so that the last step writes into x.
+  T* other = B.xt;
+  T *cx = from_zero ? nullptr : x, *cd_ = nullptr, *nd_ = B.d;
+  T* nx_ = from_zero ? ((steps & 1) ? x : other) : other;
   for (int k = 0; k < steps; ++k) {
     double cdk, crk;
     if (k == 0) {
@@ -432,7 +439,7 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
     // rotate buffers: new x becomes current; the old current x buffer is free for the next step
     T* ox = cx;
     cx = nx_;
-    nx_ = ox;
+    nx_ = ox ? ox : (cx == x ? other : x);
     T* od = cd_ ? cd_ : B.dt;
     cd_ = nd_;
     nd_ = od;
@@ -480,9 +487,11 @@ void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x,
   const int nc = phys == ELASTIC ? 2 : 1;
   TailArgs a{};
   a.nl = nlev - l0;
-  a.deg = deg;
+  a.deg = s.cdeg;
+  a.deg0 = l0 == 0 ? deg : s.cdeg;
+  a.first_level = l0;
   a.dense = 1;
-  a.coarse_steps = 8 * deg;
+  a.coarse_steps = 8 * s.cdeg;
   const Level& Lc = s.lv[nlev - 1];
   a.Ainv = phys == ELASTIC ? Lc.f32.AEi : Lc.f32.ADi;
   a.b_in = b;
@@ -527,20 +536,21 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
     if (L.dense && nlev > 1) {
       coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AEi : B.ADi, b, x);
     } else {
-      smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * deg : deg);
+      smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * s.cdeg : deg);
     }
     return;
   }
   Level& C = s.lv[l + 1];
   LevelBuf<T>& BC = C.buf<T>();
-  smooth<T>(s, st, phys, l, b, x, true, deg);
+  const int dl = l == 0 ? deg : s.cdeg;  // smoothing steps on this level
+  smooth<T>(s, st, phys, l, b, x, true, dl);
   residual_op<T>(s, st, phys, l, b, x, B.r);
   restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b,
-                  phys == DAMAGE ? C.exclD : nullptr);
+                  phys == DAMAGE ? C.exclD : nullptr, l);
   vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
   prolong_add<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, BC.x, x,
-                 phys == DAMAGE ? (l == 0 ? s.act : L.exclD) : nullptr);
-  smooth<T>(s, st, phys, l, b, x, false, deg);
+                 phys == DAMAGE ? (l == 0 ? s.act : L.exclD) : nullptr, l);
+  smooth<T>(s, st, phys, l, b, x, false, dl);
 }
 
 template <class T>
@@ -643,7 +653,8 @@ pf_status pcg_host(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, 
 template <class T>
 pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   const int pi = sizeof(T) == 8 ? 1 : 0;
-  if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == deg && s.cg_nl[phys][pi] == s.nl_active &&
+  const int degkey = deg * 1000 + s.cdeg;
+  if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == degkey && s.cg_nl[phys][pi] == s.nl_active &&
       s.cg_tail[phys][pi] == (int)s.use_tail)
     return PF_OK;
   if (s.cg_exec[phys][pi]) {
@@ -694,7 +705,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   s.cg_graph[phys][pi] = g;
   s.cg_exec[phys][pi] = ex;
   s.cg_body_kernels[phys][pi] = (int)nk;
-  s.cg_deg[phys][pi] = deg;
+  s.cg_deg[phys][pi] = degkey;
   s.cg_nl[phys][pi] = s.nl_active;
   s.cg_tail[phys][pi] = (int)s.use_tail;
   return PF_OK;
@@ -1448,6 +1459,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->am_forcing = 0.0;
   o->am_forcing_max = 1e-3;
   o->mg_tail = 1;
+  o->mg_coarse_degree = 0;
   return PF_OK;
 }
 
@@ -1557,6 +1569,7 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
   s->use_tail = o->mg_tail != 0;
+  s->cdeg = o->mg_coarse_degree > 0 ? o->mg_coarse_degree : o->mg_degree;
   pf_step_report r{};
   r.omega_bar_min = o->omega;
   pf_status status = begin_step(*s, st, *L);
@@ -1732,6 +1745,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
   s->use_tail = o->mg_tail != 0;
+  s->cdeg = o->mg_coarse_degree > 0 ? o->mg_coarse_degree : o->mg_degree;
   s->elastic_ready64 = s->elastic_ready32 = s->xu_valid = false;
   pf_step_report r{};
   pf_status status = u_solve(*s, st, *o, &r);
@@ -1754,6 +1768,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
   s->use_tail = o->mg_tail != 0;
+  s->cdeg = o->mg_coarse_degree > 0 ? o->mg_coarse_degree : o->mg_degree;
   pf_step_report r{};
   pf_status status = alpha_solve(*s, st, *o, &r);
   if (status == PF_OK || status == PF_ENOTCONV) {

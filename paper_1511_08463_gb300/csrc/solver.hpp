@@ -132,6 +132,7 @@ struct pf_sim {
   // single-block tail of the FP32 V-cycle (pf_solver_opts.mg_tail): first level per operator
   // (-1: none; -2: not computed yet) and its shared-memory bytes
   bool use_tail = true;
+  int cdeg = 2;  // Chebyshev steps per smoothing on levels >= 1 (pf_solver_opts.mg_coarse_degree)
   int tail_first[2] = {-2, -2};
   int cg_tail[2][2] = {};
   double* host = nullptr;  // pinned read-back slot from the context's pool

@@ -23,7 +23,8 @@ enum Mode : int {
   M_MASKED = 1,  // y = A_ff x_f on free dofs (x read as 0 on excluded dofs), 0 on excluded dofs
   M_RESB = 2,    // r = b - A_ff x_f on free dofs, 0 on excluded dofs
   M_RESID = 3,   // elastic physical residual r = f - K u on free dofs (u unmasked), 0 elsewhere
-  M_CHEB = 4,    // Chebyshev step: d' = cd d + cr dinv (b - A x); x' = x + d' (free dofs)
+  M_CHEB = 4,    // Chebyshev step: d' = cd d + cr dinv (b - A x); x' = x + d' (free dofs);
+                 // x == null reads x = 0 (first step from zero)
   M_GRAD = 5,    // damage: F = H x + g0, Phi, active flags, rhs = -F on the inactive set
   M_TRIAL = 6    // damage: same as M_GRAD at x_t = clip(x + mu d, lo, hi); writes x_t
 };
@@ -167,7 +168,7 @@ struct ElasticArgs {
   T* y;               // output (2n); M_CHEB: new x
   T* dout;            // M_CHEB: new d
   RedSlot slot;
-  int coarse;         // launch accounting: 1 on coarse multigrid levels
+  int coarse;         // launch accounting: multigrid level (0 = finest)
 };
 
 template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT>
@@ -197,8 +198,8 @@ struct ElasticOp {
 
   __device__ V load(int node, int X2, int Y2) const {
     V v;
-    v.ux = args.x[2 * node];
-    v.uy = args.x[2 * node + 1];
+    v.ux = args.x ? args.x[2 * node] : T(0);  // M_CHEB without x: smoothing from zero
+    v.uy = args.x ? args.x[2 * node + 1] : T(0);
     if (MODE != M_APPLY && MODE != M_RESID) {
       if (is_fixed(g, X2, Y2, 0)) v.ux = T(0);
       if (is_fixed(g, X2, Y2, 1)) v.uy = T(0);
@@ -301,7 +302,7 @@ struct DamageArgs {
   T* xt;                // M_TRIAL: trial point
   uint8_t* act;         // M_GRAD/M_TRIAL: active flags written
   RedSlot slot;
-  int coarse;           // launch accounting: 1 on coarse multigrid levels
+  int coarse;           // launch accounting: multigrid level (0 = finest)
 };
 
 template <class T, int KIND_, int MODE, bool DOT>
@@ -340,7 +341,7 @@ struct DamageOp {
       double z = double(args.x[node]) + double(args.cd) * double(args.d[node]);
       v.p = T(fmin(fmax(z, l), h));
     } else {
-      v.p = args.x[node];
+      v.p = args.x ? args.x[node] : T(0);  // M_CHEB without x: smoothing from zero
       if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = T(0);
     }
     return v;

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailArgs a) {
   const int comp_base = NC == 2 ? 0 : 2;
   for (int l = 0; l + 1 < a.nl; ++l) {  // down: pre-smooth, residual, restrict
     const TailLevel& L = a.L[l];
-    smooth<KIND, NC>(L, B[l], rec, true, a.deg);
+    smooth<KIND, NC>(L, B[l], rec, true, l == 0 ? a.deg0 : a.deg);
     TailBufs& Bl = B[l];
     apply_level<KIND, NC>(L, Bl.coef, Bl.x, rec, [&](int node, const float* f) {
 #pragma unroll
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailArgs a) {
     for (int node = tid; node < L.g.n; node += nt)
       prolong_node(L.g, C.g, NC, comp_base, B[l + 1].x, B[l].x, B[l].excl, node);
     __syncthreads();
-    smooth<KIND, NC>(L, B[l], rec, false, a.deg);
+    smooth<KIND, NC>(L, B[l], rec, false, l == 0 ? a.deg0 : a.deg);
   }
   for (int i = tid; i < NC * a.L[0].g.n; i += nt) a.x_out[i] = B[0].x[i];
 }
@@ -294,7 +294,7 @@ size_t tail_smem_limit() {
 }
 
 void tail_vcycle(cudaStream_t s, int ncomp, const TailArgs& a, size_t smem) {
-  const int id = kclass(KC_COARSE, false, true);
+  const int id = kclass(KC_TAIL, false, a.first_level);
   const bool crossed = a.L[0].g.kind == CROSSED;
   if (crossed && ncomp == 2)
     PF_LAUNCH(id, 0.0, s, pdl_launch(k_tail_vcycle<CROSSED, 2>, 1, TAIL_THREADS, smem, s, a));
