@@ -13,8 +13,8 @@
   reduced-space Newton method (Algorithm 4 on (u, alpha) with Jacobian [[K, B], [B^T, H]],
   Section 3.3) with backtracking; if Newton does not converge, return to ORAM.
 
-Readings (listed in the design notes): the Dirichlet lift is applied before the first iteration
-of every load step; the stopping rule is max|alpha^k - alpha^{k-1}| <= tol together with
+Readings where the paper is silent: the Dirichlet lift is applied before the first iteration
+of every load step (over-relaxing u across changed boundary data would overshoot them); the stopping rule is max|alpha^k - alpha^{k-1}| <= tol together with
 max|u^k - u^{k-1}| <= tol * max|u^k| (the second part catches an over-relaxed u that has not
 settled while alpha no longer moves).
 

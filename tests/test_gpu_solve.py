@@ -94,8 +94,8 @@ def test_notched_oram_load_steps():
 
 
 def test_bar_am_through_nucleation():
-    """Bar (Section 4.2) with the symmetry-breaking seed column at x = L/2 (design reading of
-    the bifurcation at nucleation); AM (omega = 1)."""
+    """Bar (Section 4.2) with a symmetry-breaking seed column near x = L/2 (at nucleation the
+    branch would otherwise be chosen by round-off); AM (omega = 1)."""
     w = W.bar(nx=64, ny=8, n_steps=20, seed_column=True)
     g, p, reps = _run_steps(w, w.loads[11:16], omega=1.0)
     for rep, r in reps:

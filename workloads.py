@@ -80,8 +80,9 @@ class Workload:
 
 
 # ---------------------------------------------------------------------------------------------
-# Critical loads used to place the load schedules (closed forms of the model stated in Section 4;
-# the plane-strain readings are derived in the design notes).  These only position the inputs.
+# Critical loads used to place the load schedules (closed forms of the model stated in Section 4,
+# in plane strain: the homogeneous states have q = E/(1-nu^2) eps^2, so the AT1 onset
+# q = 3 Gc/(8 ell) gives t_c and dT_c below).  These only position the inputs.
 # ---------------------------------------------------------------------------------------------
 def plane_strain_modulus(E: float, nu: float) -> float:
     return E / (1.0 - nu * nu)
