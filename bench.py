@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=16.0)
     ap.add_argument("--serve-only", action="store_true", help="run the serving leg alone")
+    ap.add_argument("--batch-instances", type=int, default=256,
+                    help="instances in the batch leg (0: no batch leg)")
+    ap.add_argument("--batch-workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -291,6 +294,43 @@ def serve_record(args, ctx):
     }
 
 
+def batch_record(args, ctx):
+    """Batch leg: seeded notched squares (N log-uniform on [64, 256] in multiples of 16, ell in
+    [2h, 8h], nu in [0.2, 0.35]), one load step each from rest to t ~ U[0.5, 1] (before crack
+    initiation, near t = 1.3 on these meshes), all through one pf_solve_batch call (concurrent
+    host threads, one stream each), mixed precision."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1511_08463_gb300 import sim as S
+
+    ws = W.batch_of_notched(n_instances=args.batch_instances, seed=0, t_max=1.0)
+    sims = [S.Sim(w, ctx) for w in ws]
+    opts = S.make_opts(omega=ws[0].omega, precision="mixed", batch_workers=args.batch_workers)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, reps = S.solve_batch(sims, [w.loads[0] for w in ws], opts=opts, ctx=ctx)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    secs = np.array([r["seconds"] for r in reps])
+    nodes = sum(g.n_nodes for g in sims)
+    for g in sims:
+        g.close()
+    return {
+        "instances": len(ws), "seconds": dt, "instances_per_s": len(ws) / dt,
+        "workers": args.batch_workers, "worst_status": int(st),
+        "not_converged": sum(1 for r in reps if r["status"] != 0),
+        "step_p50_ms": float(np.percentile(secs, 50) * 1e3),
+        "step_p99_ms": float(np.percentile(secs, 99) * 1e3),
+        "mean_nodes": nodes / len(ws),
+        "sample": f"{len(ws)} notched squares (seed 0), N log-uniform 64..256 (multiple of 16), "
+                  f"ell ~ U[2h, 8h], nu ~ U[0.2, 0.35], one load step each from rest to "
+                  f"t ~ U[0.5, 1] (pre-initiation), omega 1.6, mixed precision, one "
+                  f"pf_solve_batch call with {args.batch_workers} host threads",
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -443,14 +483,18 @@ def run_ours(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e!s}"[:300]}
 
-    # ---- serving leg (rank-local request loop; rank 0 reports) ---------------------------------
-    serving = None
+    # ---- serving and batch legs (rank-local; rank 0 reports) ----------------------------------
+    serving = batch = None
     n_dofs, ws_gb = 3 * sim.n_nodes, sim.workspace_bytes / 1e9
-    if args.serve_jobs > 0:
-        sim.close()  # release the 1024^2 workspace before the serving arena
+    if args.serve_jobs > 0 or args.batch_instances > 0:
+        sim.close()  # release the 1024^2 workspace first
         del sim
         torch.cuda.empty_cache()
+    if args.serve_jobs > 0:
         serving = serve_record(args, ctx)
+    if args.batch_instances > 0:
+        batch = batch_record(args, ctx)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         am_its = [r["am_iters"] for r in reps]
@@ -476,6 +520,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fp64_window": fp,
             "serving": serving,
+            "batch": batch,
             "solver": {"algo": args.algo, "am_iters_per_step": am_its,
                        "newton_iters_per_step": [r["newton_iters"] for r in reps],
                        "seconds_per_step": [round(r["seconds"], 3) for r in reps],
