@@ -96,7 +96,6 @@ class ArenaAlloc {
     }
   }
   size_t size() const { return size_; }
-  size_t used() const { return used_; }
   size_t peak() const { return peak_; }
 
  private:

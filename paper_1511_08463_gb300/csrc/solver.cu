@@ -669,7 +669,8 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   CU(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
   CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
