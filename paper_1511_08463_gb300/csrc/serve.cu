@@ -27,9 +27,14 @@
 #include <thread>
 #include <vector>
 
+#include "arena.hpp"
 #include "solver.hpp"
 
 using namespace pf;
+
+using pf::ArenaAlloc;
+using pf::ARENA_ALIGN;
+using pf::round_up;
 
 namespace {
 
@@ -49,59 +54,7 @@ pf_status fail(pf_status st, const char* fmt, ...) {
       return fail(PF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
   } while (0)
 
-constexpr size_t ARENA_ALIGN = 256;
-
-inline size_t round_up(size_t n) { return (n + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN; }
-
 inline pf_status worse(pf_status a, pf_status b) { return a > b ? a : b; }
-
-// First-fit allocator over [0, size) with coalescing of neighbouring free blocks.
-class ArenaAlloc {
- public:
-  void init(size_t size) {
-    free_.clear();
-    free_[0] = size;
-    size_ = size;
-    used_ = peak_ = 0;
-  }
-  bool alloc(size_t n, size_t* off) {
-    n = round_up(n);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < n) continue;
-      const size_t o = it->first, rem = it->second - n;
-      free_.erase(it);
-      if (rem) free_[o + n] = rem;
-      *off = o;
-      used_ += n;
-      peak_ = std::max(peak_, used_);
-      return true;
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = round_up(n);
-    used_ -= n;
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  size_t size() const { return size_; }
-  size_t peak() const { return peak_; }
-
- private:
-  std::map<size_t, size_t> free_;
-  size_t size_ = 0, used_ = 0, peak_ = 0;
-};
 
 struct Job {
   int64_t id = 0;

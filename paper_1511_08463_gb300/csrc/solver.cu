@@ -1258,7 +1258,7 @@ pf_status newton_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_s
       }
     }
     s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
-    if (!accepted) {  // restore the step's starting point
+    if (!accepted) {  // restore this Newton iteration's starting point
       CU(cudaMemcpyAsync(s.u, s.nu0, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
       CU(cudaMemcpyAsync(s.alpha, s.na0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
       vec_convert<float, double>(st, s.alpha32, s.alpha, n);
