@@ -108,6 +108,25 @@ __device__ __forceinline__ T cget(const Grid& gc, const T* v, bool centre, int I
   return v[(gc.nv + J * gc.nx + I) * ncomp + c];
 }
 
+// (P x_c)(node), component c: P1 interpolation from the nested coarse grid (weight 1 at a
+// coincident coarse node, 1/2 at the two coarse nodes of the coarse edge the fine node bisects).
+template <class T>
+__device__ __forceinline__ T prolong_value(const Grid& gf, const Grid& gc, int ncomp, const T* xc,
+                                           int node, int X2, int Y2, int c) {
+  if (node < gf.nv) {
+    int i = X2 / 2, j = Y2 / 2, I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
+    if (!pi && !pj) return cget(gc, xc, false, I, J, c, ncomp);
+    if (pi && !pj) return T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J, c, ncomp));
+    if (!pi && pj) return T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I, J + 1, c, ncomp));
+    if (gf.kind == RIGHT)
+      return T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J + 1, c, ncomp));
+    return cget(gc, xc, true, I, J, c, ncomp);
+  }
+  int cc = node - gf.nv, j = cc / gf.nx, i = cc - j * gf.nx;
+  int I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
+  return T(0.5) * (cget(gc, xc, false, I + pi, J + pj, c, ncomp) + cget(gc, xc, true, I, J, c, ncomp));
+}
+
 // x_f(node) += (P x_c)(node) (P1 interpolation), except on prescribed and excluded fine dofs.
 template <class T>
 __device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, int ncomp,
@@ -117,20 +136,7 @@ __device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, int
   node_coords(gf, node, X2, Y2);
   bool ex = excl && excl[node];
   for (int c = 0; c < ncomp; ++c) {
-    T v;
-    if (node < gf.nv) {
-      int i = X2 / 2, j = Y2 / 2, I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
-      if (!pi && !pj) v = cget(gc, xc, false, I, J, c, ncomp);
-      else if (pi && !pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J, c, ncomp));
-      else if (!pi && pj) v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I, J + 1, c, ncomp));
-      else if (gf.kind == RIGHT)
-        v = T(0.5) * (cget(gc, xc, false, I, J, c, ncomp) + cget(gc, xc, false, I + 1, J + 1, c, ncomp));
-      else v = cget(gc, xc, true, I, J, c, ncomp);
-    } else {
-      int cc = node - gf.nv, j = cc / gf.nx, i = cc - j * gf.nx;
-      int I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
-      v = T(0.5) * (cget(gc, xc, false, I + pi, J + pj, c, ncomp) + cget(gc, xc, true, I, J, c, ncomp));
-    }
+    T v = prolong_value(gf, gc, ncomp, xc, node, X2, Y2, c);
     if (ex || is_fixed(gf, X2, Y2, comp_base + c)) v = T(0);
     xf[node * ncomp + c] += v;
   }

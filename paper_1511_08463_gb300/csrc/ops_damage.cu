@@ -17,7 +17,8 @@ static double damage_bytes(const Grid& g, int mode, const DamageArgs<T>& a) {
     case M_TRIAL: node = 7 * t + 1; break;
   }
   if (a.excl) node += 1;
-  return double(g.n) * node + double(g.nelem) * t;
+  const double xc = (mode == M_CHEB && a.xc) ? double(a.gc.n) * t : 0.0;  // fused prolongation
+  return double(g.n) * node + double(g.nelem) * t + xc;
 }
 
 template <class Op>

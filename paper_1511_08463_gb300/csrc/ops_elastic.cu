@@ -16,6 +16,7 @@ static double elastic_bytes(const Grid& g, int coef, int mode, const ElasticArgs
     case M_CHEB: node = ((a.x ? 2 : 0) + (a.d ? 2 : 0) + 8) * t; break;  // b, dinv, y, d' (+ x, d)
   }
   double coefb = coef == COEF_ALPHA ? double(g.n) * t : double(g.nelem) * t;
+  if (mode == M_CHEB && a.xc) coefb += 2.0 * a.gc.n * t;  // fused prolongation: coarse x
   return double(g.n) * node + coefb;
 }
 

@@ -375,10 +375,14 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
 
 template <class T>
 void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, const T* d,
-               T* xo, T* dout, double cd, double cr) {
+               T* xo, T* dout, double cd, double cr, const T* xc = nullptr) {
   Level& L = s.lv[l];
   if (phys == ELASTIC) {
     ElasticArgs<T> a{};
+    if (xc) {
+      a.xc = xc;
+      a.gc = s.lv[l + 1].g;
+    }
     a.x = x;
     a.alpha = alpha_of<T>(s);
     a.coef = L.buf<T>().coefE;
@@ -393,6 +397,10 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_CHEB, false, false, a);
   } else {
     DamageArgs<T> a{};
+    if (xc) {
+      a.xc = xc;
+      a.gc = s.lv[l + 1].g;
+    }
     a.x = x;
     a.w = L.buf<T>().wD;
     a.excl = l == 0 ? s.act : L.exclD;
@@ -410,9 +418,11 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
 
 // Chebyshev smoothing on D_l1^{-1} A over [lmin, lmax] = [0.1, 1] (l1 scaling bounds the
 // spectrum by 1).  Starts from x (x0 == nullptr: from zero); result written to x.
+// xc (optional, not with from_zero): the coarse-grid correction, prolongated into x by the first
+// step as it reads x (x + P xc), which saves the separate prolongation launch.
 template <class T>
 void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool from_zero,
-            int steps) {
+            int steps, const T* xc = nullptr) {
   LevelBuf<T>& B = s.lv[l].buf<T>();
   const int nc = phys == ELASTIC ? 2 : 1;
   const size_t nd = (size_t)nc * s.lv[l].g.n;
@@ -435,7 +445,7 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
       crk = 2.0 * rn / delta;
       rho = rn;
     }
-    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk);
+    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk, k == 0 ? xc : nullptr);
     // rotate buffers: new x becomes current; the old current x buffer is free for the next step
     T* ox = cx;
     cx = nx_;
@@ -548,9 +558,8 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
   restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b,
                   phys == DAMAGE ? C.exclD : nullptr, l);
   vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
-  prolong_add<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, BC.x, x,
-                 phys == DAMAGE ? (l == 0 ? s.act : L.exclD) : nullptr, l);
-  smooth<T>(s, st, phys, l, b, x, false, dl);
+  // prolongation x += P x_c fused into the first post-smoothing step
+  smooth<T>(s, st, phys, l, b, x, false, dl, BC.x);
 }
 
 template <class T>

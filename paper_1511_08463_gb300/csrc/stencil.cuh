@@ -14,7 +14,7 @@
 //   DamageOp:  H p = sum_T (w_T M_T + c1 L_T) p_T with w_T = q_T + c2 (eq. helmholtz), and for
 //              the gradient E_alpha = H alpha + g0, g0_T = (c3 - q_T) |T| / 3 per node.
 #pragma once
-#include "pf_core.cuh"
+#include "mg_core.cuh"
 
 namespace pf {
 
@@ -164,6 +164,8 @@ struct ElasticArgs {
   const T* b;         // M_RESB, M_CHEB right-hand side
   const T* d;         // M_CHEB previous update
   const T* dinv;      // M_CHEB inverse diagonal (2n)
+  const T* xc;        // M_CHEB: if set, x is read as x + P xc (prolongation from grid gc fused
+  Grid gc;            // into the first post-smoothing step)
   T cd, cr;           // M_CHEB coefficients
   T* y;               // output (2n); M_CHEB: new x
   T* dout;            // M_CHEB: new d
@@ -200,6 +202,10 @@ struct ElasticOp {
     V v;
     v.ux = args.x ? args.x[2 * node] : T(0);  // M_CHEB without x: smoothing from zero
     v.uy = args.x ? args.x[2 * node + 1] : T(0);
+    if (MODE == M_CHEB && args.xc) {
+      v.ux += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0);
+      v.uy += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 1);
+    }
     if (MODE != M_APPLY && MODE != M_RESID) {
       if (is_fixed(g, X2, Y2, 0)) v.ux = T(0);
       if (is_fixed(g, X2, Y2, 1)) v.uy = T(0);
@@ -293,6 +299,8 @@ struct DamageArgs {
   const T* b;           // M_RESB, M_CHEB
   const T* d;           // M_CHEB previous update; M_TRIAL direction
   const T* dinv;        // M_CHEB
+  const T* xc;          // M_CHEB: if set, x is read as x + P xc (grid gc), see ElasticArgs
+  Grid gc;
   const double* lo;     // M_GRAD/M_TRIAL: lower bound alpha_prev
   T cd, cr;             // M_CHEB coefficients; M_TRIAL: cd = step mu
   double zeta;
@@ -342,6 +350,7 @@ struct DamageOp {
       v.p = T(fmin(fmax(z, l), h));
     } else {
       v.p = args.x ? args.x[node] : T(0);  // M_CHEB without x: smoothing from zero
+      if (MODE == M_CHEB && args.xc) v.p += prolong_value(g, args.gc, 1, args.xc, node, X2, Y2, 0);
       if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = T(0);
     }
     return v;
