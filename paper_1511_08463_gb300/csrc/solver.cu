@@ -674,8 +674,18 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   }
   Krylov<T>& K = kry<T>(s);
   const size_t nd = (size_t)(phys == ELASTIC ? 2 : 1) * s.lv[0].g.n;
+  // the graph and the capture stream are released on every early return
+  struct Owned {
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    ~Owned() {
+      if (cs) cudaStreamDestroy(cs);
+      if (g) cudaGraphDestroy(g);
+    }
+  } own;
   cudaGraph_t g;
   CU(cudaGraphCreate(&g, 0));
+  own.g = g;
   cudaGraphConditionalHandle h;
   CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
@@ -688,6 +698,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStream_t cs;
   CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  own.cs = cs;
   CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   prof_set_capturing(true);
   precond<T>(s, cs, phys, K.r, K.z, deg);
@@ -702,16 +713,14 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   cudaGraph_t captured;
   cudaError_t e1 = cudaStreamEndCapture(cs, &captured);
   cudaError_t e2 = cudaStreamDestroy(cs);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    cudaGraphDestroy(g);
+  own.cs = nullptr;
+  if (e1 != cudaSuccess || e2 != cudaSuccess)
     return fail(PF_ECUDA, "CG graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
-  }
   cudaGraphExec_t ex;
   cudaError_t e3 = cudaGraphInstantiate(&ex, g, 0);
-  if (e3 != cudaSuccess) {
-    cudaGraphDestroy(g);
+  if (e3 != cudaSuccess)
     return fail(PF_ECUDA, "CG graph instantiation failed: %s", cudaGetErrorString(e3));
-  }
+  own.g = nullptr;  // kept by the sim
   s.cg_graph[phys][pi] = g;
   s.cg_exec[phys][pi] = ex;
   s.cg_body_kernels[phys][pi] = (int)nk;
