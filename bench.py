@@ -454,25 +454,31 @@ def run_ours(args):
                 "measured_on": f"replay of load step {W0 + 1} with graph capture off"}
 
     # ---- FP64 GPU path on the first steps of the same window ------------------------------
+    # (extra legs run on single-GPU runs only; a failing extra leg reports its error in the line
+    # instead of taking the measured metric with it)
     fp = None
-    KF = min(args.fp64_steps, K)
-    if KF > 0:
-        sim.set_fields(*snap)
-        o64 = S.make_opts(algo=args.algo, omega=w.omega, precision="fp64",
-                          use_graphs=0 if args.no_graphs else 1)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        reps64 = [sim.load_step(*w.loads[k], o64, allow_notconv=True) for k in range(W0, W0 + KF)]
-        f1.record()
-        torch.cuda.synchronize()
-        t64 = f0.elapsed_time(f1) / 1e3
-        tmix = sum(r["seconds"] for r in reps[:KF])
-        err = max(abs(a["energy"][2] - b["energy"][2]) / max(abs(b["energy"][2]), 1e-300)
-                  for a, b in zip(reps[:KF], reps64))
-        fp = {"steps": f"{W0 + 1}-{W0 + KF}", "fp64_steps_per_s": KF / t64,
-              "mixed_steps_per_s": KF / tmix, "mixed_speedup": t64 / tmix,
-              "max_rel_energy_diff_mixed_vs_fp64": err}
+    KF = min(args.fp64_steps, K) if world == 1 else 0
+    try:
+        if KF > 0:
+            sim.set_fields(*snap)
+            o64 = S.make_opts(algo=args.algo, omega=w.omega, precision="fp64",
+                              use_graphs=0 if args.no_graphs else 1)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            reps64 = [sim.load_step(*w.loads[k], o64, allow_notconv=True)
+                      for k in range(W0, W0 + KF)]
+            f1.record()
+            torch.cuda.synchronize()
+            t64 = f0.elapsed_time(f1) / 1e3
+            tmix = sum(r["seconds"] for r in reps[:KF])
+            err = max(abs(a["energy"][2] - b["energy"][2]) / max(abs(b["energy"][2]), 1e-300)
+                      for a, b in zip(reps[:KF], reps64))
+            fp = {"steps": f"{W0 + 1}-{W0 + KF}", "fp64_steps_per_s": KF / t64,
+                  "mixed_steps_per_s": KF / tmix, "mixed_speedup": t64 / tmix,
+                  "max_rel_energy_diff_mixed_vs_fp64": err}
+    except Exception as e:  # report, never fake
+        fp = {"error": f"{type(e).__name__}: {e!s}"[:300]}
 
     # ---- CPU baseline -------------------------------------------------------------------------
     cpu = None
@@ -486,14 +492,22 @@ def run_ours(args):
     # ---- serving and batch legs (rank-local; rank 0 reports) ----------------------------------
     serving = batch = None
     n_dofs, ws_gb = 3 * sim.n_nodes, sim.workspace_bytes / 1e9
-    if args.serve_jobs > 0 or args.batch_instances > 0:
+    do_serve = args.serve_jobs > 0 and world == 1
+    do_batch = args.batch_instances > 0 and world == 1
+    if do_serve or do_batch:
         sim.close()  # release the 1024^2 workspace first
         del sim
         torch.cuda.empty_cache()
-    if args.serve_jobs > 0:
-        serving = serve_record(args, ctx)
-    if args.batch_instances > 0:
-        batch = batch_record(args, ctx)
+    if do_serve:
+        try:
+            serving = serve_record(args, ctx)
+        except Exception as e:  # report, never fake
+            serving = {"error": f"{type(e).__name__}: {e!s}"[:300]}
+    if do_batch:
+        try:
+            batch = batch_record(args, ctx)
+        except Exception as e:  # report, never fake
+            batch = {"error": f"{type(e).__name__}: {e!s}"[:300]}
         torch.cuda.empty_cache()
 
     if rank == 0:
