@@ -137,3 +137,37 @@ def test_thermal_no_damage_below_critical_jump():
     # an x-homogeneous band along the exposed face (small end effects of the side conditions)
     assert p.alpha[ybot].min() > 0 and p.alpha[ybot].min() >= p.alpha[~ybot].max() - 1e-12
     assert np.ptp(p.alpha[ybot]) < 0.5 * p.alpha[ybot].max()
+
+
+def test_omega_bar_midpoint_rule():
+    """Reading of Section 2.1 (Algorithm 2's omega_bar): candidates omega, (1 + omega)/2, ...;
+    the first for which alpha + omega_bar * dalpha stays in the box; omega itself when <= 1."""
+    alpha = np.array([0.2, 0.5, 0.9])
+    lo = np.array([0.2, 0.0, 0.9])
+    hi = np.ones(3)
+    dalpha = np.array([0.0, 0.3, 0.0])  # the largest feasible step is (1 - 0.5)/0.3 = 5/3
+    assert am.omega_bar(alpha, dalpha, lo, hi, 1.8) == pytest.approx(1.4)  # 1.8 -> 1.4
+    assert am.omega_bar(alpha, dalpha, lo, hi, 1.6) == pytest.approx(1.6)  # feasible as is
+    dalpha = np.array([0.0, 0.4, 0.0])  # largest feasible step 1.25: 1.8 -> 1.4 -> 1.2
+    assert am.omega_bar(alpha, dalpha, lo, hi, 1.8) == pytest.approx(1.2)
+    dalpha = np.array([0.0, -0.45, 0.0])  # towards the lower bound: step <= 0.5/0.45 = 1.11
+    assert am.omega_bar(alpha, dalpha, lo, hi, 1.8) == pytest.approx(1.1)  # 1.8 -> 1.4 -> 1.2 -> 1.1
+    assert am.omega_bar(alpha, np.array([0.0, 5.0, 0.0]), lo, hi, 0.7) == 0.7  # omega <= 1
+    # a step that is infeasible for every candidate above 1 falls back to 1 (the minimizer itself)
+    assert am.omega_bar(alpha, np.array([0.0, 0.5, 0.0]), lo, hi, 1.9) == pytest.approx(1.0, abs=1e-8)
+
+
+def test_dirichlet_lift_sets_prescribed_values_exactly():
+    """Reading: the step's data t * g are written into u before the first iteration, and only on
+    prescribed dofs."""
+    w = W.bar(nx=16, ny=2, n_steps=5)
+    p = Problem(w)
+    rng = np.random.default_rng(0)
+    p.u = rng.normal(size=p.u.shape)
+    before = p.u.reshape(-1).copy()
+    t = 0.37
+    am.begin_step(p, t, 0.0)
+    after = p.u.reshape(-1)
+    np.testing.assert_array_equal(after[p.u_fixed], t * p.u_load[p.u_fixed])
+    np.testing.assert_array_equal(after[~p.u_fixed], before[~p.u_fixed])
+    assert np.any(p.u_load[p.u_fixed] != 0)  # the bar's end displacement is a genuine load
