@@ -81,10 +81,6 @@ void l1_dinv_damage(cudaStream_t s, const Grid& g, const Mat& m, const T* w, T* 
 template <class T>
 void restrict_res(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
                   const T* rf, T* bc, const uint8_t* excl_c, int level);  // excl_c may be null
-// xf += P xc on free components; excl (fine, may be null) zeroes excluded nodes
-template <class T>
-void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                 const T* xc, T* xf, const uint8_t* excl, int level);
 
 // ---- coarsest level dense solve -----------------------------------------------------------------
 template <class T>

@@ -505,26 +505,6 @@ template void restrict_res<double>(cudaStream_t, const Grid&, const Grid&, int, 
 template void restrict_res<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
                                   float*, const uint8_t*, int);
 
-template <class T>
-__global__ void k_prolong(Grid gf, Grid gc, int ncomp, int comp_base, const T* xc, T* xf,
-                          const uint8_t* excl) {
-  pdl_enter();
-  int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= gf.n) return;
-  prolong_node(gf, gc, ncomp, comp_base, xc, xf, excl, node);
-}
-template <class T>
-void prolong_add(cudaStream_t s, const Grid& gf, const Grid& gc, int ncomp, int comp_base,
-                 const T* xc, T* xf, const uint8_t* excl, int level) {
-  // read the coarse correction, read and write the fine iterate (+ fine mask bytes)
-  const double bytes = double(ncomp) * sizeof(T) * (gc.n + 2.0 * gf.n) + (excl ? double(gf.n) : 0.0);
-  PF_LAUNCH(kclass(KC_TRANSFER, sizeof(T) == 8, level), bytes, s,
-            pdl_launch(k_prolong<T>, nblocks(gf.n), RED_THREADS, 0, s, gf, gc, ncomp, comp_base, xc, xf, excl));
-}
-template void prolong_add<double>(cudaStream_t, const Grid&, const Grid&, int, int, const double*,
-                                  double*, const uint8_t*, int);
-template void prolong_add<float>(cudaStream_t, const Grid&, const Grid&, int, int, const float*,
-                                 float*, const uint8_t*, int);
 
 // ---------------------------------------------------------------------------------------------
 // coarsest level: dense assembly, Cholesky and triangular solves in one thread block
