@@ -1579,10 +1579,13 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   if (!s || !L) return fail(PF_EINVAL, "null argument");
   TRY(check_opts(o));
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
-  if (s->busy) return fail(PF_EBUSY, "sim busy");
+  bool idle = false;
+  if (!s->busy.compare_exchange_strong(idle, true)) return fail(PF_EBUSY, "sim busy");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  CU(cudaSetDevice(s->ctx->device));
-  s->busy = true;
+  if (cudaError_t e = cudaSetDevice(s->ctx->device); e != cudaSuccess) {
+    s->busy = false;
+    return fail(PF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  }
   auto t0 = std::chrono::steady_clock::now();
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -117,7 +118,7 @@ struct pf_sim {
   bool xu_valid = false;
   int xu_precision = -1;
   size_t ws_used = 0;
-  bool busy = false;
+  std::atomic<bool> busy{false};  // a load step is running (PF_EBUSY for a second caller)
   // CUDA graphs holding one whole PCG solve each (device-side while loop), per operator
   // (elastic, damage) and precision (FP32, FP64); rebuilt if the smoothing degree or the number of
   // levels in use changes
