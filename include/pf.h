@@ -194,7 +194,9 @@ pf_status pf_set_material(pf_sim* sim, const pf_material* m);
 /* Solve one load step (Algorithm 1/2/3 according to o->algo) on `stream`, in place on the
  * resident state: alpha_prev <- alpha, Dirichlet data t*load written into u, then iterate to
  * convergence.  Blocks the host until the step finishes (convergence decisions are read back).
- * On PF_ENOTCONV the last iterate is kept and the state stays valid. rep may be NULL. */
+ * On PF_ENOTCONV the last iterate is kept and the state stays valid. rep may be NULL.
+ * PF_EBUSY if another thread is running a load step on the same sim (different sims may run
+ * concurrently from different threads, each on its own stream). */
 pf_status pf_load_step(pf_sim* sim, const pf_load* L, const pf_solver_opts* o, void* stream,
                        pf_step_report* rep);
 
