@@ -86,3 +86,42 @@ def test_solver_opts_layout_matches_header(lib):
     assert [f for f, _ in B.pf_solver_opts._fields_] == list(expect)
     for k, v in expect.items():
         assert getattr(o, k) == v, k
+
+
+def test_header_is_plain_c_and_links(tmp_path, lib):
+    """include/pf.h compiles as C99 (no C++-only constructs), and a C caller links against
+    libpf.so and calls the host-only entry points."""
+    import shutil
+    import subprocess
+
+    from paper_1511_08463_gb300 import _build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "caller.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "pf.h"
+int main(void) {
+  pf_solver_opts o;
+  pf_mesh_desc d;
+  if (pf_default_opts(&o) != PF_OK || o.algo != PF_ALGO_ORAM) return 1;
+  memset(&d, 0, sizeof d);
+  d.kind = PF_MESH_CROSSED; d.nx = 64; d.ny = 64; d.lx = 1.0; d.ly = 1.0;
+  if (pf_workspace_bytes(&d, PF_MIXED) == 0) return 2;
+  d.nx = 0;
+  if (pf_workspace_bytes(&d, PF_MIXED) != 0) return 3;
+  printf("%s\n", pf_version());
+  return 0;
+}
+''')
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_build.LIB)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lpf",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.startswith("libpf")
