@@ -86,11 +86,16 @@ def _merit_gradient(x, F, J, lo, hi, bounded):
 
 
 def rs_solve(F, J, x0, lo, hi, bounded, zeta=1e-10, atol=0.0, rtol=1e-12, maxit=200,
-             linsolve=None, c_armijo=1e-4, mu_min=2.0 ** -20):
+             linsolve=None, c_armijo=1e-4, mu_min=2.0 ** -20,
+             directions=("newton", "steepest")):
     """Algorithm 4 for MCP(F, lo, hi).  F(x) -> vector, J(x) -> sparse Jacobian.
 
-    Returns (x, info) with info = dict(its, phi0, phi, status) and status in
-    {"converged", "maxit", "linesearch"}.
+    directions: the search directions tried in order in every iteration ("newton": the reduced
+    Newton step of eq. reducednewton; "steepest": minus the gradient of ||Phi||^2 / 2).
+
+    Returns (x, info) with info = dict(its, phi0, phi, status, steepest) and status in
+    {"converged", "maxit", "linesearch"}; steepest counts the iterations whose accepted step
+    came from the steepest-descent direction.
     """
     if linsolve is None:
         linsolve = lambda A, b: spla.spsolve(A.tocsc(), b)
@@ -100,6 +105,7 @@ def rs_solve(F, J, x0, lo, hi, bounded, zeta=1e-10, atol=0.0, rtol=1e-12, maxit=
     nphi0 = float(np.linalg.norm(Phi))
     tol = atol + rtol * nphi0
     its = 0
+    n_steepest = 0
     status = "converged"
     while float(np.linalg.norm(Phi)) > tol:
         if its >= maxit:
@@ -118,7 +124,7 @@ def rs_solve(F, J, x0, lo, hi, bounded, zeta=1e-10, atol=0.0, rtol=1e-12, maxit=
         d[up] = hi[up] - x[up]
         m0 = float(Phi @ Phi)
         accepted = False
-        for direction in ("newton", "steepest"):
+        for direction in directions:
             if direction == "steepest":
                 d = -_merit_gradient(x, Fx, Jx, lo, hi, bounded)
             mu = 1.0
@@ -132,12 +138,14 @@ def rs_solve(F, J, x0, lo, hi, bounded, zeta=1e-10, atol=0.0, rtol=1e-12, maxit=
                     break
                 mu *= 0.5
             if accepted:
+                n_steepest += direction == "steepest"
                 break
         if not accepted:
             status = "linesearch"
             break
         x, Fx, Phi = xt, Ft, Pt
-    return x, dict(its=its, phi0=nphi0, phi=float(np.linalg.norm(Phi)), status=status)
+    return x, dict(its=its, phi0=nphi0, phi=float(np.linalg.norm(Phi)), status=status,
+                   steepest=n_steepest)
 
 
 def box_qp(H, g, x0, lo, hi, zeta=1e-10, rtol=1e-13, atol=0.0, maxit=200):

@@ -254,3 +254,35 @@ def test_galerkin_coarse_operator_is_mean_of_children(kind):
     Hc = fe.damage_hessian_from_weight(mat, gc, wc).toarray()
     Pd = P.toarray()
     np.testing.assert_allclose(Pd.T @ Hf @ Pd, Hc, atol=1e-13 * np.abs(Hc).max())
+
+
+def test_thermal_temperature_at_centroids_against_hand_values():
+    """eq. (tempfielderfc) at element centroids, against values worked by hand from the printed
+    erf table (tests/golden/thermal_centroid_temperature.json): catches a wrong penetration
+    scaling (erfc(x2/pen) vs erfc(x2/(2 pen))), a wrong sign, or x2 not measured from y0."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "thermal_centroid_temperature.json")
+    with open(path) as fh:
+        gold = json.load(fh)
+    for case in gold["cases"]:
+        m = case["mesh"]
+        mesh = Mesh(m["kind"], m["nx"], m["ny"], m["x0"], m["y0"], m["lx"], m["ly"])
+        geo = fe.Geometry(mesh)
+        mat = fe.Material(beta=1.0, pen=case["pen"])
+        T = fe.temperature(mat, geo, case["dT"])
+        height = geo.centroid[:, 1] - m["y0"]
+        table = case["centroid_height_to_T"]
+        seen = set()
+        for e in range(T.size):
+            k = int(np.argmin([abs(height[e] - h) for h, _ in table]))
+            assert abs(height[e] - table[k][0]) < 1e-12, f"unexpected centroid height {height[e]}"
+            assert abs(T[e] - table[k][1]) <= 2e-10 * case["dT"], (e, T[e], table[k])
+            seen.add(k)
+        assert seen == set(range(len(table)))
+        # the eigenstrain is beta T on both normal components, no shear (eq. energytshock)
+        e0 = fe.eigenstrain(mat, geo, case["dT"])
+        np.testing.assert_array_equal(e0[:, 0], T)
+        np.testing.assert_array_equal(e0[:, 1], T)
+        assert not np.any(e0[:, 2])

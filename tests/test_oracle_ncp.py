@@ -92,3 +92,79 @@ def test_damage_qp_against_bruteforce_on_tiny_mesh():
     a, info = am.solve_alpha(p, u, lo.copy(), 0.0)
     ab = box_qp_bruteforce(H, g0, lo, np.ones_like(lo))
     np.testing.assert_allclose(a, ab, atol=1e-10)
+
+
+def _random_mcp(seed, n=24, n_free=5):
+    """A strictly convex QP's gradient F = Hx + g with box bounds on all but n_free components."""
+    rng = np.random.default_rng(seed)
+    A = sp.random(n, n, density=0.25, random_state=seed, format="csr")
+    H = (A @ A.T + sp.eye(n) * 0.5).tocsr()
+    g = rng.normal(size=n)
+    lo = rng.uniform(-1.0, 0.0, n)
+    hi = lo + rng.uniform(0.3, 1.5, n)
+    bounded = np.ones(n, dtype=bool)
+    bounded[rng.choice(n, n_free, replace=False)] = False
+    return H, g, lo, hi, bounded, rng
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_merit_gradient_matches_central_differences(seed):
+    """grad(||Phi||^2 / 2) of the steepest-descent fallback of Algorithm 4 against central
+    differences, at points where both nested Fischer-Burmeister arguments are nonzero (Phi is
+    smooth there).  Points inside the box, on a bound with the gradient pushing outwards, and
+    outside the box; unbounded components use Phi = F."""
+    from oracle.ncp import _merit_gradient
+
+    H, g, lo, hi, bounded, rng = _random_mcp(seed)
+    n = g.size
+    merit = lambda x: 0.5 * float(np.sum(mcp_residual(x, H @ x + g, lo, hi, bounded) ** 2))
+    for where in ("inside", "on_lower", "outside"):
+        if where == "inside":
+            x = lo + rng.uniform(0.2, 0.8, n) * (hi - lo)
+        elif where == "on_lower":
+            x = lo.copy()
+        else:
+            x = hi + rng.uniform(0.1, 0.3, n)
+        x[~bounded] = rng.normal(size=int((~bounded).sum()))
+        F = H @ x + g
+        # stay away from the kink of phi: both arguments of each nested phi nonzero
+        psi = phi_fb(hi - x, -F)
+        ok = bounded & ((np.abs(hi - x) + np.abs(F)) > 1e-3) & ((np.abs(x - lo) + np.abs(psi)) > 1e-3)
+        assert ok[bounded].all()
+        grad = _merit_gradient(x, F, H, lo, hi, bounded)
+        h = 1e-6
+        fd = np.array([(merit(x + h * e) - merit(x - h * e)) / (2 * h) for e in np.eye(n)])
+        np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(fd).max()))
+
+
+def test_steepest_descent_fallback_branch_reaches_the_kkt_point():
+    """Algorithm 4's fallback: when the Newton search fails (here a planted bad linear solve
+    returning a zero step on the first iteration), the steepest-descent direction of
+    the merit function is taken; the iteration still ends at the brute-force KKT point."""
+    from oracle.ncp import rs_solve
+
+    rng = np.random.default_rng(3)
+    n = 6
+    A = rng.normal(size=(n, n))
+    H = sp.csr_matrix(A @ A.T + 0.5 * np.eye(n))
+    g = rng.normal(size=n) * 2
+    lo = rng.uniform(-1.0, 0.0, n)
+    hi = lo + rng.uniform(0.2, 1.5, n)
+    calls = {"n": 0}
+
+    def bad_first(Ann, b):
+        calls["n"] += 1
+        d = np.linalg.solve(Ann.toarray(), b)
+        return 0.0 * d if calls["n"] == 1 else d
+
+    bounded = np.ones(n, dtype=bool)
+    x0 = np.clip(rng.normal(size=n), lo, hi)
+    x, info = rs_solve(lambda x: H @ x + g, lambda x: H, x0, lo, hi, bounded, rtol=1e-13,
+                       linsolve=bad_first)
+    assert info["status"] == "converged" and info["steepest"] >= 1
+    np.testing.assert_allclose(x, box_qp_bruteforce(H, g, lo, hi), atol=1e-10)
+    # steepest descent alone (no Newton direction): every step accepted, ||Phi|| reduced
+    x1, info1 = rs_solve(lambda x: H @ x + g, lambda x: H, x0, lo, hi, bounded, rtol=1e-3,
+                         maxit=200, directions=("steepest",))
+    assert info1["status"] in ("converged", "maxit") and info1["steepest"] == info1["its"]
+    assert info1["phi"] < 0.1 * info1["phi0"]
