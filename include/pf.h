@@ -20,6 +20,9 @@
  *  - "device pointer" arguments are CUDA global-memory addresses on the sim's device; "host
  *    pointer" arguments are ordinary CPU memory.  The caller owns every buffer it passes.
  *  - stream arguments are cudaStream_t values passed as void* (NULL = legacy default stream).
+ *  - every function taking a pf_sim claims that sim for the duration of the call: a second call
+ *    on the same sim from another thread while it runs returns PF_EBUSY and does nothing.
+ *    pf_destroy, which cannot report this, must not overlap any other call on its sim.
  *  - node order: the (nx+1)(ny+1) vertex grid row-major (x fastest), then, for crossed meshes,
  *    the nx*ny cell-centre grid row-major.  u is interleaved (u_x, u_y) per node.
  *  - doubled grid units: vertex (i, j) sits at (2i, 2j), the centre of cell (i, j) at
@@ -195,8 +198,8 @@ pf_status pf_set_material(pf_sim* sim, const pf_material* m);
  * resident state: alpha_prev <- alpha, Dirichlet data t*load written into u, then iterate to
  * convergence.  Blocks the host until the step finishes (convergence decisions are read back).
  * On PF_ENOTCONV the last iterate is kept and the state stays valid. rep may be NULL.
- * PF_EBUSY if another thread is running a load step on the same sim (different sims may run
- * concurrently from different threads, each on its own stream). */
+ * PF_EBUSY if another thread is using the same sim (different sims may run concurrently from
+ * different threads, each on its own stream). */
 pf_status pf_load_step(pf_sim* sim, const pf_load* L, const pf_solver_opts* o, void* stream,
                        pf_step_report* rep);
 
@@ -283,6 +286,7 @@ pf_status pf_set_fields(pf_sim* sim, const double* u, const double* alpha,
 /* Mesh sizes: nodes, elements and multigrid levels. */
 pf_status pf_sim_info(const pf_sim* sim, int64_t* n_nodes, int64_t* n_elements, int32_t* levels);
 
+/* Release the sim (not its workspace).  No other call on the sim may run at the same time. */
 void pf_destroy(pf_sim* sim);
 
 /* ---------------------------------------------------------------------------------------------
@@ -349,9 +353,11 @@ pf_status pf_op_full_residual(pf_sim* sim, double* phi_norm, void* stream);
  * device pointers owned by the caller, node order as above.  out: host, 3 doubles.
  * Scratch: a fixed 328 KB array compiled into the library, held on every device that loads it
  * until the process exits.  Limit: at most 8192 cell rows (ny); larger meshes return PF_EINVAL
- * with a message.  The first call on a device looks up the array's device address (do this
- * first call before any stream capture).  All calls on a device share the array and reuse its
- * previous contents, so calls that overlap on the GPU race; serialize them.  Synchronous. */
+ * with a message.  The first call on a device looks up the array's device address and keeps it
+ * (a cudaDeviceReset of that device invalidates it: do not use the library on a device after
+ * resetting it).  All calls on a device share the array and reuse its previous contents, so
+ * calls that overlap on the GPU race; serialize them.  Synchronous: every call waits for its
+ * stream, so it cannot be recorded into a CUDA graph by stream capture. */
 pf_status pf_energy_noalloc(const pf_mesh_desc* d, const pf_material* m, const pf_load* L,
                             const double* u, const double* alpha, double out[3], void* stream);
 

@@ -35,6 +35,8 @@ double* g_dev_ptr[MAX_DEVICES] = {};
 
 // Device address of the scratch array for the current device (looked up once per device; the
 // host-side name g_noalloc_scratch is only a stand-in and must never be passed to a kernel).
+// A cudaDeviceReset of the device unloads the module, so the cached address is then stale: the
+// library must not be used on a device after it has been reset.
 pf_status scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -104,8 +106,10 @@ extern "C" pf_status pf_energy_noalloc(const pf_mesh_desc* d, const pf_material*
   const bool thermal = mi->beta != 0.0 && L->dT != 0.0;
   double* eig = scr + EIG_OFFSET;
   if (e == cudaSuccess && thermal) {
-    int cnt = g.ny * elems_per_cell(g.kind);
-    k_eig_rows<<<(cnt + 255) / 256, 256, 0, s>>>(eig, g.ny, g.kind, g.hy, mi->beta, L->dT, mi->pen);
+    const int cnt = g.ny * elems_per_cell(g.kind);
+    PF_LAUNCH(kclass(KC_SETUP, true, 0), 8.0 * cnt, s,
+              pdl_launch(k_eig_rows, dim3((cnt + 255) / 256), dim3(256), 0, s, eig, g.ny, g.kind,
+                         g.hy, mi->beta, L->dT, mi->pen));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

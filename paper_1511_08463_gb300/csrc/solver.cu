@@ -37,6 +37,12 @@ static bool debug_enabled() {
   static const bool on = getenv("PF_DEBUG") && getenv("PF_DEBUG")[0] == '1';
   return on;
 }
+// PF_TRACE=1 prints one line per alternate-minimization iteration on stderr (damage change,
+// relative displacement change, omega_bar, cumulative Krylov counts)
+static bool trace_enabled() {
+  static const bool on = getenv("PF_TRACE") && getenv("PF_TRACE")[0] == '1';
+  return on;
+}
 #define CU(call)                                                                       \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
@@ -50,6 +56,24 @@ static bool debug_enabled() {
     pf_status s_ = (expr);           \
     if (s_ != PF_OK) return s_;      \
   } while (0)
+
+// Exclusive use of a sim for the duration of one entry point: a second caller on the same sim
+// gets PF_EBUSY instead of racing on its fields, reduction slots and work buffers.
+struct SimClaim {
+  pf_sim* s;
+  bool ok;
+  explicit SimClaim(pf_sim* sim) : s(sim) {
+    bool idle = false;
+    ok = s->busy.compare_exchange_strong(idle, true);
+  }
+  ~SimClaim() {
+    if (ok) s->busy = false;
+  }
+};
+#define CLAIM(sim)                                             \
+  SimClaim claim_(sim);                                        \
+  if (!claim_.ok) return fail(PF_EBUSY, "sim busy")
+
 
 // ---------------------------------------------------------------------------------------------
 // workspace arena
@@ -1069,6 +1093,10 @@ pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& oin,
   *da_out = da;
   *durel_out = du[1] > 0.0 ? du[0] / du[1] : du[0];
   if (rep) rep->omega_bar_min = std::min(rep->omega_bar_min, wbar);
+  if (trace_enabled())
+    fprintf(stderr, "[pf-am] da %.3e du %.3e wbar %.4f cg_u %lld cg_a %lld rs %d\n", da,
+            *durel_out, wbar, rep ? (long long)rep->cg_iters_u : 0LL,
+            rep ? (long long)rep->cg_iters_alpha : 0LL, rep ? rep->rs_iters : 0);
   return PF_OK;
 }
 
@@ -1528,6 +1556,7 @@ pf_status pf_create_mesh(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws
 
 pf_status pf_set_material(pf_sim* s, const pf_material* mi) {
   if (!s || !mi) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!(mi->E > 0) || !(mi->Gc > 0) || !(mi->ell > 0) || !(mi->k_ell >= 0) || !(mi->nu > -1.0) ||
       !(mi->nu < 0.5))
     return fail(PF_EINVAL, "invalid material constants");
@@ -1579,13 +1608,10 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   if (!s || !L) return fail(PF_EINVAL, "null argument");
   TRY(check_opts(o));
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
-  bool idle = false;
-  if (!s->busy.compare_exchange_strong(idle, true)) return fail(PF_EBUSY, "sim busy");
+  CLAIM(s);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaError_t e = cudaSetDevice(s->ctx->device); e != cudaSuccess) {
-    s->busy = false;
+  if (cudaError_t e = cudaSetDevice(s->ctx->device); e != cudaSuccess)
     return fail(PF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-  }
   auto t0 = std::chrono::steady_clock::now();
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
@@ -1604,12 +1630,12 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   r.status = status;
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rep) *rep = r;
-  s->busy = false;
   return status;
 }
 
 pf_status pf_energy(pf_sim* s, void* stream, double out[3]) {
   if (!s || !out) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   return energy_now(*s, static_cast<cudaStream_t>(stream), out);
@@ -1617,6 +1643,7 @@ pf_status pf_energy(pf_sim* s, void* stream, double out[3]) {
 
 pf_status pf_get_fields(pf_sim* s, double* u, double* alpha, double* alpha_prev) {
   if (!s) return fail(PF_EINVAL, "null sim");
+  CLAIM(s);
   CU(cudaSetDevice(s->ctx->device));
   CU(cudaDeviceSynchronize());
   size_t n = s->lv[0].g.n;
@@ -1628,6 +1655,7 @@ pf_status pf_get_fields(pf_sim* s, double* u, double* alpha, double* alpha_prev)
 
 pf_status pf_set_fields(pf_sim* s, const double* u, const double* alpha, const double* alpha_prev) {
   if (!s) return fail(PF_EINVAL, "null sim");
+  CLAIM(s);
   CU(cudaSetDevice(s->ctx->device));
   size_t n = s->lv[0].g.n;
   if (u) CU(cudaMemcpy(s->u, u, 2 * n * sizeof(double), cudaMemcpyHostToDevice));
@@ -1653,6 +1681,7 @@ void pf_destroy(pf_sim* s) { delete s; }
 
 pf_status pf_set_load(pf_sim* s, const pf_load* L) {
   if (!s || !L) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   TRY(set_load(*s, L->t, L->dT, 0));
@@ -1663,6 +1692,7 @@ pf_status pf_set_load(pf_sim* s, const pf_load* L) {
 pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* x, void* y,
                               void* stream) {
   if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
@@ -1689,6 +1719,7 @@ pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* 
 
 pf_status pf_op_elastic_residual(pf_sim* s, double* r, double* norm2, void* stream) {
   if (!s || !r) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   double nrm;
@@ -1700,6 +1731,7 @@ pf_status pf_op_elastic_residual(pf_sim* s, double* r, double* norm2, void* stre
 pf_status pf_op_damage_gradient(pf_sim* s, double* F, double* Phi, uint8_t* active,
                                 double* phi_norm2, void* stream) {
   if (!s || !F || !Phi) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
@@ -1712,6 +1744,7 @@ pf_status pf_op_damage_gradient(pf_sim* s, double* F, double* Phi, uint8_t* acti
 
 pf_status pf_op_damage_apply(pf_sim* s, int precision, const void* x, void* y, void* stream) {
   if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
@@ -1740,6 +1773,7 @@ pf_status pf_op_damage_apply(pf_sim* s, int precision, const void* x, void* y, v
 pf_status pf_op_coupling_apply(pf_sim* s, int transpose, const double* x, double* y,
                                void* stream) {
   if (!s || !x || !y) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   if (transpose != 0 && transpose != 1) return fail(PF_EINVAL, "transpose must be 0 or 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1758,6 +1792,7 @@ pf_status pf_op_coupling_apply(pf_sim* s, int transpose, const double* x, double
 
 pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_step_report* rep) {
   if (!s) return fail(PF_EINVAL, "null sim");
+  CLAIM(s);
   TRY(check_opts(o));
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1781,6 +1816,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
 
 pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_step_report* rep) {
   if (!s) return fail(PF_EINVAL, "null sim");
+  CLAIM(s);
   TRY(check_opts(o));
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1806,6 +1842,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
 
 pf_status pf_op_full_residual(pf_sim* s, double* phi_norm, void* stream) {
   if (!s || !phi_norm) return fail(PF_EINVAL, "null argument");
+  CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   return full_residual(*s, static_cast<cudaStream_t>(stream), 1e-10, phi_norm);
