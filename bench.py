@@ -30,6 +30,34 @@ if ROOT not in sys.path:
 METRIC = "load steps/s at 1024^2 mesh (notched square, ORAM omega=1.5), mixed vs FP64 GPU"
 UNIT = "load_steps/s"
 L2_BYTES = 126.5e6
+# load steps (1-based) of the 50-step schedule in which the damage grows: the crack starts from
+# the notch at step 33, grows slowly to a near-critical state at step 34 and runs through the
+# ligament at step 35; every timed sample holds them
+GROWTH_STEPS = (33, 34, 35, 36)
+# steps repeated in plain FP64 to measure the mixed-precision error on damage-growth steps
+FP64_STEPS = (33, 36)
+# iteration cap of alternate minimization: near-critical steps need well over 2000 iterations at
+# 1024^2 (the paper's own AM counts reach 3382, Table 3)
+AM_MAXIT = 20000
+
+
+def select_steps(nsched: int, first: int, k: int, growth) -> list:
+    """K schedule indices (0-based) from first .. nsched-1: all of them if K covers the range,
+    else the damage-growth steps plus evenly spaced others, sorted."""
+    avail = list(range(first, nsched))
+    if k >= len(avail):
+        return avail
+    g = [s - 1 for s in growth if first <= s - 1 < nsched][:k]
+    rest = [s for s in avail if s not in g]
+    m = k - len(g)
+    pick = set()
+    for i in range(m):
+        pick.add(rest[int(round(i * (len(rest) - 1) / max(m - 1, 1)))] if m > 1 else rest[len(rest) // 2])
+    for s in rest:  # rounding may have picked one twice
+        if len(pick) >= m:
+            break
+        pick.add(s)
+    return sorted(set(g) | pick)
 
 
 def parse():
@@ -42,7 +70,8 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--algo", choices=["ORAM", "ORAM_N"], default="ORAM",
                     help="ORAM (Algorithm 2) or ORAM-N (Algorithm 3)")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="damage-growth steps repeated in plain FP64 (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven CG loops (per-kernel profilers cannot see inside graphs)")
@@ -50,7 +79,7 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=32,
                     help="jobs in the serving sample (0: no serving leg)")
     ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrivals per second")
-    ap.add_argument("--serve-max-n", type=int, default=256, help="largest serving mesh N")
+    ap.add_argument("--serve-max-n", type=int, default=1024, help="largest serving mesh N")
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=16.0)
     ap.add_argument("--serve-only", action="store_true", help="run the serving leg alone")
@@ -157,16 +186,53 @@ def iterations_lower_bound(omega: float, tol: float) -> int:
     return int(math.ceil(math.log(tol) / math.log(abs(1.0 - omega)))) + 1
 
 
-def cpu_baseline_record(size: int, omega: float, tol: float, step_index: int):
+BAR_FULL_RUN = r"""
+import sys, time, json
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+from oracle import am
+from oracle.problem import Problem
+w = W.bar()
+p = Problem(w)
+t0 = time.perf_counter()
+its = 0
+for (t, dT) in w.loads:
+    r = am.load_step(p, t, dT, omega=w.omega, tol=1e-6)
+    its += r["its"]
+print(json.dumps({"seconds": time.perf_counter() - t0, "steps": len(w.loads), "its": its}))
+"""
+
+
+def oracle_bar_full_run():
+    """Full oracle run of the 128 x 16 bar (Section 4.2, 20 load steps, AM, tol 1e-6), single
+    thread: seconds, steps and AM iterations."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", BAR_FULL_RUN, ROOT], capture_output=True, text=True,
+                       env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(size: int, step_index: int, am_iters_per_step: float):
+    """The oracle (FP64, sparse LU, single thread) on the metric's workload: its time per ORAM
+    iteration at size^2 extrapolated from one iteration at 128^2 and 256^2, times the mean AM
+    iteration count per timed load step that the GPU run measured.  A full measured oracle run of
+    the 128 x 16 bar is reported beside it."""
     it_s, t, p = oracle_iteration_seconds(size, step_index)
-    n_it = iterations_lower_bound(omega, tol)
-    return {"value": 1.0 / (it_s * n_it), "unit": UNIT, "cores": 1, "kind": "oracle",
+    bar = oracle_bar_full_run()
+    return {"value": 1.0 / (it_s * am_iters_per_step), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "extrapolated": True,
+            "bar_128x16_full_run": {"seconds": bar["seconds"], "load_steps": bar["steps"],
+                                    "am_iters": bar["its"],
+                                    "load_steps_per_s": bar["steps"] / bar["seconds"]},
             "sample": (f"one ORAM iteration of the FP64 oracle (sparse LU solves) at 128^2 "
                        f"({t[128]:.1f}s) and 256^2 ({t[256]:.1f}s), load step {step_index + 1}; "
                        f"time per iteration extrapolated to {size}^2 with the fitted size exponent "
-                       f"{p:.2f} ({it_s:.0f}s), times {n_it} iterations per load step (the ORAM "
-                       f"contraction bound |1-omega|^k <= tol of a step without damage growth, a "
-                       f"lower bound, so the baseline is optimistic); extrapolated")}
+                       f"{p:.2f} ({it_s:.0f}s), times the GPU run's mean of "
+                       f"{am_iters_per_step:.1f} AM iterations per timed load step; extrapolated. "
+                       f"Measured in full: the 128x16 bar, 20 load steps, {bar['its']} AM "
+                       f"iterations in {bar['seconds']:.1f}s")}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -259,7 +325,8 @@ def serve_record(args, ctx):
     """Serving leg: a seeded Poisson stream of notched-square and bar jobs (N log-uniform on
     [32, serve_max_n], 10-60 load steps each, mixed precision) through the libpf request loop;
     per-load-step latency = end of the step minus the moment it became ready (arrival for the
-    first step), so admission and worker queueing are included."""
+    first step), so admission and worker queueing are included.  Jobs with N <= 64 are run again
+    alone in plain FP64 afterwards, and their per-step energies compared."""
     import numpy as np
 
     import workloads as W
@@ -270,27 +337,57 @@ def serve_record(args, ctx):
     arena = int(args.serve_arena_gb * 1e9)
     srv = S.Server(arena, workers=args.serve_workers, ctx=ctx)
     t0 = srv.now()
-    ids = [srv.submit(j.workload, opts=S.make_opts(omega=j.workload.omega, precision="mixed"),
-                      arrival=t0 + j.arrival, fields=False) for j in jobs]
+    mk = lambda w, prec: S.make_opts(omega=w.omega, precision=prec, am_maxit=AM_MAXIT)
+    ids = [srv.submit(j.workload, opts=mk(j.workload, "mixed"), arrival=t0 + j.arrival,
+                      fields=False) for j in jobs]
     res = [srv.wait(i) for i in ids]
     st = srv.stats()
     srv.close()
     lat = np.concatenate([r["latency"] for r in res])
+    ok = [r["status"] == 0 for r in res]
+    lat_ok = np.concatenate([r["latency"] for r, g in zip(res, ok) if g] or [np.zeros(0)])
     svc = np.array([rep["seconds"] for r in res for rep in r["reports"]])
     makespan = max(r["finished"] for r in res) - t0
     last_arrival = max(r["arrival"] for r in res) - t0
+    failed = []
+    for j, r in zip(jobs, res):
+        if r["status"] != 0:
+            bad = [k for k, rep in enumerate(r["reports"]) if rep["status"] != 0]
+            failed.append({"job": j.job_id, "workload": j.workload.name, "status": r["status"],
+                           "steps_done": r["steps_done"], "steps": len(j.workload.loads),
+                           "first_failing_step": bad[0] + 1 if bad else None})
+    # FP64 reference runs of the small jobs, alone and in order
+    errs = []
+    for j, r in zip(jobs, res):
+        w = j.workload
+        if max(w.nx, w.ny) > 64 or r["status"] != 0:
+            continue
+        g = S.Sim(w, ctx)
+        o = mk(w, "fp64")
+        e = []
+        for rep, ld in zip(r["reports"], w.loads):
+            r64 = g.load_step(*ld, o, allow_notconv=True)
+            e.append(abs(rep["energy"][2] - r64["energy"][2]) / abs(r64["energy"][2]))
+        g.close()
+        errs.append(max(e))
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3) if a.size else None
     return {
-        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "service_p50_ms": float(np.percentile(svc, 50) * 1e3),
-        "service_p99_ms": float(np.percentile(svc, 99) * 1e3),
+        "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+        "p50_ms_converged_jobs": pct(lat_ok, 50), "p99_ms_converged_jobs": pct(lat_ok, 99),
+        "service_p50_ms": pct(svc, 50), "service_p99_ms": pct(svc, 99),
         "steps": int(lat.size), "steps_per_s": float(lat.size / makespan),
         "makespan_s": makespan, "last_arrival_s": last_arrival, "jobs": len(jobs),
-        "jobs_not_ok": sum(1 for r in res if r["status"] != 0),
+        "jobs_not_ok": len(failed), "failed_jobs": failed,
+        "max_rel_energy_err_vs_fp64": max(errs) if errs else None,
+        "fp64_checked_jobs": len(errs),
         "workers": st["workers"], "max_active": st["max_active"],
         "arena_gb": st["arena_bytes"] / 1e9, "arena_peak_gb": st["arena_peak"] / 1e9,
+        "sizes": sorted(max(j.workload.nx, j.workload.ny) for j in jobs),
         "sample": f"{len(jobs)} jobs, Poisson rate {args.serve_rate}/s (seed 0), notched squares "
                   f"and bars, N log-uniform 32..{args.serve_max_n} (multiple of 16), 10-60 load "
-                  f"steps each, mixed precision, default tolerances",
+                  f"steps each, mixed precision, default tolerances, am_maxit {AM_MAXIT}; "
+                  f"energy error: every step of each converged job with N <= 64 against the same "
+                  f"job run alone in plain FP64",
     }
 
 
@@ -364,7 +461,7 @@ def run_ours(args):
     ctx = S.Context(local)
     sim = S.Sim(w, ctx)
     opts = S.make_opts(algo=args.algo, omega=w.omega, precision=args.precision,
-                       use_graphs=0 if args.no_graphs else 1)
+                       use_graphs=0 if args.no_graphs else 1, am_maxit=AM_MAXIT)
     log(args, f"[rank {rank}] nodes {sim.n_nodes} levels {sim.levels} workspace "
               f"{sim.workspace_bytes / 1e9:.2f} GB; warm-up {W0} steps")
     # warm-up: the first W0 steps
@@ -377,7 +474,8 @@ def run_ours(args):
     # CUDA events on the launching stream (events cannot bracket single launches in a graph)
     lib.pf_prof_reset()
     lib.pf_prof_enable(1, -1)
-    popts = S.make_opts(algo=args.algo, omega=w.omega, precision=args.precision, use_graphs=0)
+    popts = S.make_opts(algo=args.algo, omega=w.omega, precision=args.precision, use_graphs=0,
+                        am_maxit=AM_MAXIT)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     sim.load_step(*w.loads[W0], popts, allow_notconv=True)
@@ -390,44 +488,62 @@ def run_ours(args):
     sim.set_fields(*snap)
     torch.cuda.synchronize()
 
-    # ---- timed region (CUDA graphs on) ---------------------------------------------------------
-    # One pass over the K steps serves both measurements.  Each step: copy the state in from
-    # pinned host memory (e2e only), the load step itself, copy the state back (e2e only).
-    # value: sum of the device-event intervals around the load steps alone (state resident);
-    # e2e: events around the whole pass including the host<->device copies.
+    # ---- main pass over the schedule (CUDA graphs on) -------------------------------------------
+    # Every step from W0+1 on runs in order, so each step starts from the state its predecessor
+    # left.  The K timed steps are a stratified sample that always holds the damage-growth steps
+    # (select_steps).  A timed step: copy the state in from pinned host memory (e2e only), the
+    # load step, copy the state back (e2e only).  value: sum of the device-event intervals around
+    # the timed load steps alone (state resident); e2e: events around copy-in, step and copy-out.
+    timed = select_steps(nsched, W0, K, GROWTH_STEPS)
+    last = max(timed)
+    fp64_at = [k - 1 for k in FP64_STEPS if W0 <= k - 1 <= last] or [timed[0]]
     n = sim.n_nodes
     hu = torch.empty((n, 2), dtype=torch.float64, pin_memory=True)
     ha = torch.empty(n, dtype=torch.float64, pin_memory=True)
     hp = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    hu.numpy()[:] = snap[0]
-    ha.numpy()[:] = snap[1]
-    hp.numpy()[:] = snap[2]
     lib.pf_prof_reset()
     clocks = Clocks(local)
     barrier()
     torch.cuda.synchronize()
-    e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(K)]
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(4)] for k in timed}
     launches0 = lib.pf_launch_count()
-    e_all0.record()
-    reps = []
-    for i, k in enumerate(range(W0, W0 + K)):
-        B.check(lib.pf_set_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
-        step_ev[i][0].record()
-        reps.append(sim.load_step(*w.loads[k], opts, allow_notconv=True))
-        step_ev[i][1].record()
-        B.check(lib.pf_get_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
-    e_all1.record()
+    reps = {}
+    before, after = {}, {}  # states around the steps the FP64 leg repeats
+    synced = False  # the pinned host copy holds the current state
+    for k in range(W0, last + 1):
+        if k in fp64_at:
+            before[k] = sim.get_fields()
+        if k in ev:
+            if not synced:  # refresh the host copy (outside the timed region)
+                B.check(lib.pf_get_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
+            e = ev[k]
+            e[0].record()
+            B.check(lib.pf_set_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
+            e[1].record()
+            reps[k] = sim.load_step(*w.loads[k], opts, allow_notconv=True)
+            e[2].record()
+            B.check(lib.pf_get_fields(sim.h, hu.data_ptr(), ha.data_ptr(), hp.data_ptr()))
+            e[3].record()
+            synced = True
+        else:
+            reps[k] = sim.load_step(*w.loads[k], opts, allow_notconv=True)
+            synced = False
+        if k in fp64_at:
+            after[k] = sim.get_fields()
+        log(args, f"[rank {rank}] step {k + 1}: {reps[k]['am_iters']} AM iterations, "
+                  f"{reps[k]['seconds']:.2f} s, status {reps[k]['status']}"
+                  f"{' (timed)' if k in ev else ''}")
     torch.cuda.synchronize()
     barrier()
     launches = lib.pf_launch_count() - launches0
     clk = clocks.stop()
-    elapsed = sum(a.elapsed_time(b) for a, b in step_ev) / 1e3
+    elapsed = sum(ev[k][1].elapsed_time(ev[k][2]) for k in timed) / 1e3
     elapsed_max = aggregate_max(elapsed)
     value = K * world / elapsed_max
-    e2e_el = aggregate_max(e_all0.elapsed_time(e_all1) / 1e3)
+    e2e_el = aggregate_max(sum(ev[k][0].elapsed_time(ev[k][3]) for k in timed) / 1e3)
     e2e_value = K * world / e2e_el
+    run_steps = list(range(W0, last + 1))
+    sched_s = sum(reps[k]["seconds"] for k in run_steps)
 
     # roofline of the dominant kernel class (from the timing replay)
     import json as _json
@@ -453,30 +569,39 @@ def run_ours(args):
                 "share_of_replay_step": d["ms"] / 1e3 / replay_s,
                 "measured_on": f"replay of load step {W0 + 1} with graph capture off"}
 
-    # ---- FP64 GPU path on the first steps of the same window ------------------------------
+    # ---- FP64 GPU path on damage-growth steps ------------------------------------------------
+    # Each repeated step starts from the state the mixed run started it from; reported per step:
+    # both times, the relative energy difference and the max-norm field differences.
     # (extra legs run on single-GPU runs only; a failing extra leg reports its error in the line
     # instead of taking the measured metric with it)
     fp = None
-    KF = min(args.fp64_steps, K) if world == 1 else 0
     try:
-        if KF > 0:
-            sim.set_fields(*snap)
+        if world == 1 and args.fp64_steps > 0:
             o64 = S.make_opts(algo=args.algo, omega=w.omega, precision="fp64",
-                              use_graphs=0 if args.no_graphs else 1)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record()
-            reps64 = [sim.load_step(*w.loads[k], o64, allow_notconv=True)
-                      for k in range(W0, W0 + KF)]
-            f1.record()
-            torch.cuda.synchronize()
-            t64 = f0.elapsed_time(f1) / 1e3
-            tmix = sum(r["seconds"] for r in reps[:KF])
-            err = max(abs(a["energy"][2] - b["energy"][2]) / max(abs(b["energy"][2]), 1e-300)
-                      for a, b in zip(reps[:KF], reps64))
-            fp = {"steps": f"{W0 + 1}-{W0 + KF}", "fp64_steps_per_s": KF / t64,
-                  "mixed_steps_per_s": KF / tmix, "mixed_speedup": t64 / tmix,
-                  "max_rel_energy_diff_mixed_vs_fp64": err}
+                              use_graphs=0 if args.no_graphs else 1, am_maxit=AM_MAXIT)
+            rows = []
+            for k in fp64_at[:args.fp64_steps]:
+                sim.set_fields(*before[k])
+                torch.cuda.synchronize()
+                r64 = sim.load_step(*w.loads[k], o64, allow_notconv=True)
+                u64, a64, _ = sim.get_fields()
+                um, am_, _ = after[k]
+                rm = reps[k]
+                rows.append({
+                    "step": k + 1, "fp64_s": r64["seconds"], "mixed_s": rm["seconds"],
+                    "mixed_speedup": r64["seconds"] / rm["seconds"],
+                    "am_iters_fp64": r64["am_iters"], "am_iters_mixed": rm["am_iters"],
+                    "status_fp64": r64["status"], "status_mixed": rm["status"],
+                    "rel_energy_diff": abs(rm["energy"][2] - r64["energy"][2]) / abs(r64["energy"][2]),
+                    "u_maxnorm_rel_diff": float(np.abs(um - u64).max() / np.abs(u64).max()),
+                    "alpha_maxnorm_diff": float(np.abs(am_ - a64).max())})
+            fp = {"steps": [r["step"] for r in rows], "per_step": rows,
+                  "fp64_steps_per_s": len(rows) / sum(r["fp64_s"] for r in rows),
+                  "mixed_steps_per_s": len(rows) / sum(r["mixed_s"] for r in rows),
+                  "mixed_speedup": sum(r["fp64_s"] for r in rows) / sum(r["mixed_s"] for r in rows),
+                  "max_rel_energy_diff_mixed_vs_fp64": max(r["rel_energy_diff"] for r in rows),
+                  "max_u_maxnorm_rel_diff": max(r["u_maxnorm_rel_diff"] for r in rows),
+                  "max_alpha_maxnorm_diff": max(r["alpha_maxnorm_diff"] for r in rows)}
     except Exception as e:  # report, never fake
         fp = {"error": f"{type(e).__name__}: {e!s}"[:300]}
 
@@ -484,7 +609,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline_record(args.size, w.omega, 1e-6, W0)
+            mean_its = sum(reps[k]["am_iters"] for k in timed) / len(timed)
+            cpu = cpu_baseline_record(args.size, W0, mean_its)
         except Exception as e:  # report, never fake
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e!s}"[:300]}
@@ -511,7 +637,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     if rank == 0:
-        am_its = [r["am_iters"] for r in reps]
+        tr = [reps[k] for k in timed]
+        run = [reps[k] for k in run_steps]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W0, "ms_per_step": elapsed_max / K * 1e3, "higher_is_better": True,
@@ -520,31 +647,44 @@ def run_ours(args):
             "config": {
                 "workload": f"notched_square_{args.size}_crossed_AT1_{args.algo}_omega1.5",
                 "mesh": f"{args.size}x{args.size} crossed P1", "dofs": n_dofs,
-                "load_steps": f"{W0 + 1}-{W0 + K} of {nsched} (t up to {w.loads[-1][0]})",
+                "load_steps": (f"{len(timed)} timed of steps {W0 + 1}-{last + 1} of {nsched} "
+                               f"(t up to {w.loads[-1][0]}): {[k + 1 for k in timed]}; the "
+                               f"damage-growth steps {list(GROWTH_STEPS)} are always timed"),
                 "precision": args.precision, "parallelism": f"replicas x{world}",
-                "cuda_graphs": not args.no_graphs,
+                "cuda_graphs": not args.no_graphs, "am_maxit": AM_MAXIT,
                 "l2": f"inputs larger than L2: resident state + work buffers "
                       f"{ws_gb:.2f} GB per replica"},
             "clocks": clk, "gpu_launches": int(launches),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n, "steps": K,
-                    "how": "same pass as value: state copied in from pinned host memory before and "
-                           "out after every load step, inside the timed region"},
+                    "how": "per timed step: state copied in from pinned host memory, the load step, "
+                           "state copied out, all inside the CUDA-event interval"},
+            "schedule": {"steps": f"{W0 + 1}-{last + 1}", "load_steps_per_s": len(run_steps) / sched_s,
+                         "seconds": sched_s, "not_ok": sum(1 for r in run if r["status"] != 0),
+                         "how": "every step of the range run in order; host clock around each "
+                                "pf_load_step"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "fp64_window": fp,
             "serving": serving,
             "batch": batch,
-            "solver": {"algo": args.algo, "am_iters_per_step": am_its,
-                       "newton_iters_per_step": [r["newton_iters"] for r in reps],
-                       "seconds_per_step": [round(r["seconds"], 3) for r in reps],
-                       "minres_iters": sum(r["krylov_iters_newton"] for r in reps),
-                       "cg_u": sum(r["cg_iters_u"] for r in reps),
-                       "cg_alpha": sum(r["cg_iters_alpha"] for r in reps),
-                       "rs_iters": sum(r["rs_iters"] for r in reps),
-                       "u_solves_reused": sum(r["u_solves_reused"] for r in reps),
-                       "not_converged_steps": sum(1 for r in reps if r["status"] != 0),
-                       "final_energy": reps[-1]["energy"]},
+            "solver": {"algo": args.algo, "timed_steps": [k + 1 for k in timed],
+                       "am_iters_per_step": [r["am_iters"] for r in tr],
+                       "newton_iters_per_step": [r["newton_iters"] for r in tr],
+                       "seconds_per_step": [round(r["seconds"], 3) for r in tr],
+                       "status_per_step": [r["status"] for r in tr],
+                       "phi_rel_per_step": [r["phi_norm"] / r["phi_start"] if r["phi_start"] > 0
+                                            else 0.0 for r in tr],
+                       "omega_bar_min_per_step": [r["omega_bar_min"] for r in tr],
+                       "minres_iters": sum(r["krylov_iters_newton"] for r in tr),
+                       "cg_u": sum(r["cg_iters_u"] for r in tr),
+                       "cg_alpha": sum(r["cg_iters_alpha"] for r in tr),
+                       "rs_iters": sum(r["rs_iters"] for r in tr),
+                       "u_solves_reused": sum(r["u_solves_reused"] for r in tr),
+                       "subproblems_not_converged": sum(r["u_notconv"] + r["alpha_notconv"]
+                                                        for r in run),
+                       "not_converged_steps": sum(1 for r in run if r["status"] != 0),
+                       "final_energy": reps[last]["energy"]},
             "kernel_classes_replay_step": {k: {"ms": round(v["ms"], 3),
                                                "launches": v["launches"]}
                                            for k, v in sorted(prof_tab.items(),

@@ -144,9 +144,15 @@ typedef struct pf_solver_opts {
                             * step on every level */
   int32_t mg_coarse_degree; /* Chebyshev steps per smoothing on the coarse levels (0 (default):
                              * mg_degree) */
+  int32_t omega_rule;      /* damage over-relaxation step (Algorithm 2): 0 (default) the
+                            * recursive midpoint rule of Section 2.1 (omega, (1+omega)/2, ... until
+                            * the update stays in the box); 1: always omega, then projection onto
+                            * the box [alpha_prev, 1] */
 } pf_solver_opts;
 
-/* Per-step report (all counts summed over the step). */
+/* Per-step report (all counts summed over the step).  phi_start / phi_norm: ||Phi||_2 of the
+ * full optimality system (eq. kkt: E_u on free dofs, MCP residual of E_alpha on [alpha_prev, 1])
+ * after the Dirichlet lift at the start of the step and at its end. */
 typedef struct pf_step_report {
   int32_t status, am_iters, rs_iters, newton_iters;
   int64_t cg_iters_u, cg_iters_alpha, krylov_iters_newton, outer_refinements;
@@ -155,6 +161,13 @@ typedef struct pf_step_report {
   double seconds;
   int64_t u_solves_reused; /* AM iterations whose u-subproblem had the same alpha and load as the
                               previous one, so its minimizer was reused instead of re-solved */
+  int64_t u_notconv;       /* u-subproblem solves that stopped at their iteration cap */
+  int64_t newton_steepest; /* ORAM-N Newton iterations whose accepted step came from the
+                              steepest-descent fallback of Algorithm 4 */
+  int64_t alpha_notconv;   /* damage-subproblem solves (Algorithm 4) that stopped at their
+                              iteration cap or with a failed line search; the stopping test of
+                              the load step is accepted only after an iteration whose two
+                              subproblems both converged */
 } pf_step_report;
 
 typedef struct pf_ctx pf_ctx;
@@ -300,13 +313,15 @@ pf_status pf_set_load(pf_sim* sim, const pf_load* L);
 
 /* y = K(alpha) x for the elasticity operator E_uu (Section 1.2, eq. elasticity) with the
  * resident alpha.  x, y: device pointers to 2*n_nodes values, double when precision ==
- * PF_FP64, float when PF_MIXED (then alpha is read from its FP32 copy).  masked != 0 applies
- * the operator of the free dofs: x is read as 0 on prescribed dofs and y = x there. */
+ * PF_FP64, float when PF_MIXED (then alpha is read from its FP32 copy), aligned to one (u_x, u_y)
+ * pair (16 bytes for double, 8 for float; PF_EINVAL otherwise).  masked != 0 applies the
+ * operator of the free dofs: x is read as 0 on prescribed dofs and y is 0 there. */
 pf_status pf_op_elastic_apply(pf_sim* sim, int precision, int masked, const void* x, void* y,
                               void* stream);
 
 /* r = -(E_u) = f - K(alpha) u on free dofs, 0 on prescribed dofs, for the resident u, alpha and
- * the current load (thermal load vector included).  r: device, 2*n_nodes doubles.
+ * the current load (thermal load vector included).  r: device, 2*n_nodes doubles, 16-byte
+ * aligned (PF_EINVAL otherwise).
  * *norm2 (host) receives ||r||^2. */
 pf_status pf_op_elastic_residual(pf_sim* sim, double* r, double* norm2, void* stream);
 

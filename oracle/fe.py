@@ -95,6 +95,21 @@ def coefficient_mean(mat: Material, geo: Geometry, alpha: np.ndarray) -> np.ndar
     return 1.0 - 2.0 * m + s + mat.k_ell
 
 
+def mode_I_displacement(mat: Material, KI: float, dx, dy):
+    """Asymptotic Mode-I crack-tip displacement of linear elastic fracture mechanics, eq.
+    (surfingloading) of Section 4.1: u = KI/(2 mu) sqrt(r/(2 pi)) (kappa - cos theta)
+    (cos(theta/2), sin(theta/2)), with (r, theta) the polar coordinates of (dx, dy) around the tip
+    (theta in (-pi, pi], theta = pi on the crack line behind the tip).  kappa = (3 - nu)/(1 + nu)
+    as printed (plane stress); 3 - 4 nu for plane strain.  Returns (u_x, u_y)."""
+    dx = np.asarray(dx, dtype=float)
+    dy = np.asarray(dy, dtype=float)
+    kappa = (3.0 - mat.nu) / (1.0 + mat.nu) if mat.plane == "stress" else 3.0 - 4.0 * mat.nu
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    amp = KI / (2.0 * mat.mu) * np.sqrt(r / (2.0 * np.pi)) * (kappa - np.cos(th))
+    return amp * np.cos(0.5 * th), amp * np.sin(0.5 * th)
+
+
 def temperature(mat: Material, geo: Geometry, dT: float) -> np.ndarray:
     """T at element centroids, eq. (tempfielderfc) with x2 measured from the exposed face y=y0."""
     y = geo.centroid[:, 1] - geo.mesh.y0

@@ -77,6 +77,17 @@ class Problem:
         return hi
 
     def lift(self, t: float):
-        """Write the step's Dirichlet data t*g into u."""
+        """Write the step's Dirichlet data into u: t*g, or, for a moving Mode-I crack (Section
+        4.1, eq. surfingloading), g * u_bar(x - x_tip0 - v t, y - y_line)."""
         uf = self.u.reshape(-1)
-        uf[self.u_fixed] = t * self.u_load[self.u_fixed]
+        if self.w.mode_I is None:
+            uf[self.u_fixed] = t * self.u_load[self.u_fixed]
+            return
+        from .fe import mode_I_displacement
+
+        m = self.w.mode_I
+        dx = self.mesh.xy[:, 0] - (m["x_tip0"] + m["v"] * t)
+        dy = self.mesh.xy[:, 1] - m["y_line"]
+        ux, uy = mode_I_displacement(self.mat, m["KI"], dx, dy)
+        ub = np.stack([ux, uy], axis=1).reshape(-1)
+        uf[self.u_fixed] = self.u_load[self.u_fixed] * ub[self.u_fixed]

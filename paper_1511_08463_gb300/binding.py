@@ -51,7 +51,7 @@ class pf_solver_opts(C.Structure):
                 ("minres_rtol", C.c_double), ("use_graphs", C.c_int32),
                 ("batch_workers", C.c_int32), ("am_forcing", C.c_double),
                 ("am_forcing_max", C.c_double), ("mg_tail", C.c_int32),
-                ("mg_coarse_degree", C.c_int32)]
+                ("mg_coarse_degree", C.c_int32), ("omega_rule", C.c_int32)]
 
 
 class pf_step_report(C.Structure):
@@ -61,7 +61,9 @@ class pf_step_report(C.Structure):
                 ("outer_refinements", C.c_int64), ("dalpha_inf", C.c_double),
                 ("du_rel", C.c_double), ("phi_norm", C.c_double), ("phi_start", C.c_double),
                 ("omega_bar_min", C.c_double), ("energy", C.c_double * 3),
-                ("seconds", C.c_double), ("u_solves_reused", C.c_int64)]
+                ("seconds", C.c_double), ("u_solves_reused", C.c_int64),
+                ("u_notconv", C.c_int64), ("newton_steepest", C.c_int64),
+                ("alpha_notconv", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -10,11 +10,20 @@ static inline unsigned nblocks(size_t n, int bs = RED_THREADS) {
   size_t b = (n + bs - 1) / bs;
   return (unsigned)(b < 1 ? 1 : b);
 }
-// reduction kernels use a grid-stride loop over at most MAX_RED_BLOCKS blocks
+// Reduction kernels use a grid-stride loop over at most RED_GRID_CAP blocks (4 per SM): every
+// block adds one ticket atomic and one partial that the last block sums, so a grid sized to the
+// vector would spend more time in that serial tail than in streaming the vector.
+constexpr size_t RED_GRID_CAP = 4 * 152;
+static_assert(RED_GRID_CAP <= MAX_RED_BLOCKS, "partial buffers hold MAX_RED_BLOCKS blocks");
 static inline unsigned rblocks(size_t n) {
   size_t b = (n + RED_THREADS - 1) / RED_THREADS;
-  if (b > MAX_RED_BLOCKS) b = MAX_RED_BLOCKS;
+  if (b > RED_GRID_CAP) b = RED_GRID_CAP;
   return (unsigned)(b < 1 ? 1 : b);
+}
+// float vectors are streamed as float4 when both operands are 16-byte aligned
+template <class T>
+__device__ __forceinline__ bool vec4_ok(const void* a, const void* b) {
+  return sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -86,9 +95,20 @@ template <class T>
 __global__ void k_dot(const T* x, const T* y, size_t n, RedSlot slot) {
   pdl_enter();
   T v[1] = {T(0)};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    v[0] += x[i] * y[i];
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (vec4_ok<T>(x, y)) {
+      const float4* x4 = reinterpret_cast<const float4*>(x);
+      const float4* y4 = reinterpret_cast<const float4*>(y);
+      for (size_t i = t0; i < n / 4; i += st) {
+        const float4 a = x4[i], b = y4[i];
+        v[0] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+      }
+      done = n / 4 * 4;
+    }
+  }
+  for (size_t i = done + t0; i < n; i += st) v[0] += x[i] * y[i];
   block_reduce_finalize<1, false, T>(v, slot);
 }
 template <class T>
@@ -107,8 +127,27 @@ __global__ void k_cg_xr(T* x, T* r, const T* p, const T* Ap, size_t n, const dou
   __syncthreads();
   const T at = sa;
   T v[1] = {T(0)};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  size_t done = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (vec4_ok<T>(x, r) && vec4_ok<T>(p, Ap)) {
+      float4* x4 = reinterpret_cast<float4*>(x);
+      float4* r4 = reinterpret_cast<float4*>(r);
+      const float4* p4 = reinterpret_cast<const float4*>(p);
+      const float4* a4 = reinterpret_cast<const float4*>(Ap);
+      for (size_t i = t0; i < n / 4; i += st) {
+        float4 xv = x4[i], rv = r4[i];
+        const float4 pv = p4[i], av = a4[i];
+        xv.x += at * pv.x; xv.y += at * pv.y; xv.z += at * pv.z; xv.w += at * pv.w;
+        rv.x -= at * av.x; rv.y -= at * av.y; rv.z -= at * av.z; rv.w -= at * av.w;
+        x4[i] = xv;
+        r4[i] = rv;
+        v[0] += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+      }
+      done = n / 4 * 4;
+    }
+  }
+  for (size_t i = done + t0; i < n; i += st) {
     x[i] += at * p[i];
     T ri = r[i] - at * Ap[i];
     r[i] = ri;

@@ -1056,7 +1056,7 @@ pf_status begin_step(pf_sim& s, cudaStream_t st, const pf_load& L) {
 // max|alpha^k - alpha^{k-1}| and the relative displacement change.
 pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& oin,
                          pf_step_report* rep, double omega, double da_prev, double* da_out,
-                         double* durel_out) {
+                         double* durel_out, bool* sub_ok) {
   const Grid& g = s.lv[0].g;
   const size_t n2 = 2 * (size_t)g.n;
   // inexact subproblem solves: tolerances follow the last damage change
@@ -1074,6 +1074,10 @@ pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& oin,
     if (st1 != PF_OK && st1 != PF_ENOTCONV) return st1;
     s.xu_valid = st1 == PF_OK;
     s.xu_precision = o.precision;
+    if (st1 == PF_ENOTCONV) {
+      *sub_ok = false;
+      if (rep) rep->u_notconv++;
+    }
   } else if (rep) {
     rep->u_solves_reused++;
   }
@@ -1082,10 +1086,14 @@ pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& oin,
   TRY(read_scalars(s, st, S_DU, 2, du));
   pf_status st2 = alpha_solve(s, st, o, rep);
   if (st2 != PF_OK && st2 != PF_ENOTCONV) return st2;
+  if (st2 == PF_ENOTCONV) {
+    *sub_ok = false;
+    if (rep) rep->alpha_notconv++;
+  }
   omega_star(st, g, s.alpha, s.xrs, s.alpha_prev, slot(s, S_OMEGA));
   double ms;
   TRY(read_scalars(s, st, S_OMEGA, 1, &ms));
-  double wbar = choose_omega_bar(omega, -ms);
+  double wbar = oin.omega_rule == 1 ? omega : choose_omega_bar(omega, -ms);
   relax_alpha(st, g, s.alpha, s.xrs, s.alpha_prev, wbar, s.alpha32, slot(s, S_DALPHA));
   double da;
   TRY(read_scalars(s, st, S_DALPHA, 1, &da));
@@ -1105,7 +1113,8 @@ pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step
   double da_prev = HUGE_VAL;
   for (int k = 1; k <= o.am_maxit; ++k) {
     double da, durel;
-    TRY(oram_iteration(s, st, o, rep, omega, da_prev, &da, &durel));
+    bool sub_ok = true;
+    TRY(oram_iteration(s, st, o, rep, omega, da_prev, &da, &durel, &sub_ok));
     // with inexact solves a small change may only mean a loose solve did not move the state:
     // the test counts only for an iteration run at (nearly) the exact tolerances, i.e. one
     // whose predecessor already met the damage-change criterion
@@ -1116,9 +1125,11 @@ pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step
       rep->dalpha_inf = da;
       rep->du_rel = durel;
     }
-    if (exact && da <= o.am_tol && durel <= o.am_tol) return PF_OK;
+    // the stopping test is accepted only after an iteration whose subproblems both converged
+    if (exact && sub_ok && da <= o.am_tol && durel <= o.am_tol) return PF_OK;
   }
-  return PF_ENOTCONV;
+  return fail(PF_ENOTCONV, "alternate minimization: %d iterations, |dalpha| %.3e", o.am_maxit,
+              rep ? rep->dalpha_inf : -1.0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1204,7 +1215,9 @@ pf_status minres(pf_sim& s, cudaStream_t st, float* b, float* x, double rtol, in
   block_prec(s, st, r1, y, deg);
   double beta1;
   TRY(dot3(s, st, r1, y, &beta1));
-  if (!(beta1 >= 0.0)) return fail(PF_ENUMERIC, "MINRES: preconditioner not positive definite");
+  // a preconditioner that is not positive definite in FP32 (near-singular crack band) gives no
+  // Newton direction: reported as non-convergence, so that the caller falls back
+  if (!(beta1 >= 0.0)) return fail(PF_ENOTCONV, "MINRES: preconditioner not positive definite");
   beta1 = sqrt(beta1);
   if (beta1 == 0.0) return PF_OK;
   CU(cudaMemcpyAsync(r2, r1, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -1224,7 +1237,7 @@ pf_status minres(pf_sim& s, cudaStream_t st, float* b, float* x, double rtol, in
     oldb = beta;
     double bb;
     TRY(dot3(s, st, r2, y, &bb));
-    if (!(bb >= 0.0)) return fail(PF_ENUMERIC, "MINRES: preconditioner not positive definite");
+    if (!(bb >= 0.0)) return fail(PF_ENOTCONV, "MINRES: preconditioner not positive definite");
     beta = sqrt(bb);
     const double oldeps = epsln;
     const double delta = cs * dbar + sn * alfa;
@@ -1261,6 +1274,46 @@ pf_status coupled_residual(pf_sim& s, cudaStream_t st, double zeta, double* nrm)
   return PF_OK;
 }
 
+// Steepest-descent direction of ||Phi||^2 / 2 for the coupled system (the fallback of Algorithm
+// 4 when the Newton search fails), at the state whose residuals coupled_residual left in r64
+// (= -E_u on free dofs) and F (= E_alpha).  With Phi_u = E_u and the nested Fischer-Burmeister
+// Phi_alpha, a generalized Jacobian is G = D + R J (D, R diagonal: 0 and 1 on displacement dofs,
+// pa - pb qa and -pb qb on damage nodes; J = [[K, B], [B^T, H]] the Hessian of the energy on free
+// displacement dofs and all damage nodes).  J is symmetric, so G^T Phi = D Phi + J (R Phi).
+// Writes -G^T Phi into (du, da).  FP64 throughout.
+void coupled_merit_direction(pf_sim& s, cudaStream_t st, double* du, double* da) {
+  const Grid& g = s.lv[0].g;
+  const size_t n = g.n, n2 = 2 * n;
+  double *vu = s.tmpa, *va = s.xtr, *dga = s.Phitr, *hva = s.Ftr;
+  vec_lincomb<double>(st, vu, -1.0, s.r64, 0.0, nullptr, 0.0, n2);  // R Phi on u: Phi_u = E_u
+  merit_parts(st, g, s.alpha, s.F, s.alpha_prev, va, dga);          // R Phi and D Phi on alpha
+  ElasticArgs<double> ea{};
+  ea.x = vu;
+  ea.alpha = s.alpha;
+  ea.y = du;
+  launch_elastic<double>(st, g, s.m, COEF_ALPHA, M_MASKED, false, false, ea);  // K_ff vu
+  CouplingArgs<double> b{};
+  b.u = s.u;
+  b.alpha = s.alpha;
+  b.eig = s.thermal ? s.eig : nullptr;
+  b.excl = nullptr;
+  b.accumulate = 1;
+  b.x = va;
+  b.y = du;
+  launch_coupling<double>(st, g, s.m, false, b);  // + B va
+  b.accumulate = 0;
+  b.x = vu;
+  b.y = da;
+  launch_coupling<double>(st, g, s.m, true, b);  // B^T vu
+  DamageArgs<double> dm{};
+  dm.x = va;
+  dm.w = s.lv[0].f64.wD;
+  dm.y = hva;
+  launch_damage<double>(st, g, s.m, M_APPLY, false, dm);  // H va
+  vec_lincomb<double>(st, da, -1.0, hva, -1.0, dga, -1.0, n);
+  vec_lincomb<double>(st, du, -1.0, du, 0.0, nullptr, 0.0, n2);
+}
+
 // Algorithm 4 on the coupled system: reduced Newton steps with a projected line search on
 // ||Phi||^2.  Returns PF_OK when ||Phi|| <= tol, PF_ENOTCONV otherwise (state = best point).
 pf_status newton_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep,
@@ -1283,26 +1336,48 @@ pf_status newton_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_s
     vec_convert<float, double>(st, xs, s.r64, n2);
     vec_convert<float, double>(st, xs + n2, s.rhs, n);
     int64_t kits = 0;
-    TRY(minres(s, st, xs, xs, o.minres_rtol, o.minres_maxit, o.mg_degree, &kits));
+    const pf_status ms = minres(s, st, xs, xs, o.minres_rtol, o.minres_maxit, o.mg_degree, &kits);
+    if (ms != PF_OK && ms != PF_ENOTCONV) return ms;
+    const bool have_newton = ms == PF_OK;  // else only the steepest-descent direction is tried
     if (rep) rep->krylov_iters_newton += kits;
+    double mu_acc = 0.0;
     vec_convert<double, float>(st, s.ndu, xs, n2);
     vec_convert<double, float>(st, s.nda, xs + n2, n);
     snap_active(st, g, s.act, s.alpha, s.alpha_prev, s.nda);
-    // projected line search (alpha clipped to its box; u unbounded)
+    // projected line search (alpha clipped to its box; u unbounded) along the Newton direction,
+    // then, if it fails, along the steepest-descent direction of ||Phi||^2 / 2
     CU(cudaMemcpyAsync(s.nu0, s.u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(s.na0, s.alpha, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     bool accepted = false;
+    int dir_acc = -1;
     const double phi2 = phi * phi;
-    for (double mu = 1.0; mu >= 0x1p-20; mu *= 0.5) {
-      newton_trial(st, g, s.u, s.nu0, s.ndu, s.alpha, s.na0, s.nda, s.alpha_prev, s.alpha32, mu);
-      double pt;
-      TRY(coupled_residual(s, st, o.zeta, &pt));
-      if (pt * pt <= (1.0 - 2.0 * 1e-4 * mu) * phi2) {
-        phi = pt;
-        accepted = true;
-        break;
+    for (int dir = have_newton ? 0 : 1; dir < 2 && !accepted; ++dir) {
+      if (dir == 1) {
+        // residuals at the iteration's starting point, then the merit gradient there
+        CU(cudaMemcpyAsync(s.u, s.nu0, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(s.alpha, s.na0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        double p0;
+        TRY(coupled_residual(s, st, o.zeta, &p0));
+        coupled_merit_direction(s, st, s.ndu, s.nda);
+      }
+      for (double mu = 1.0; mu >= 0x1p-20; mu *= 0.5) {
+        newton_trial(st, g, s.u, s.nu0, s.ndu, s.alpha, s.na0, s.nda, s.alpha_prev, s.alpha32, mu);
+        double pt;
+        TRY(coupled_residual(s, st, o.zeta, &pt));
+        if (pt * pt <= (1.0 - 2.0 * 1e-4 * mu) * phi2) {
+          phi = pt;
+          accepted = true;
+          mu_acc = mu;
+          dir_acc = dir;
+          break;
+        }
       }
     }
+    if (accepted && dir_acc == 1 && rep) rep->newton_steepest++;
+    if (trace_enabled())
+      fprintf(stderr, "[pf-newton] it %d phi %.4e -> %.4e minres %lld mu %g %s\n", it,
+              sqrt(phi2), phi, (long long)kits, mu_acc,
+              accepted ? (dir_acc == 0 ? "newton" : "steepest") : "failed");
     s.elastic_ready64 = s.elastic_ready32 = s.xu_valid = false;
     if (!accepted) {  // restore this Newton iteration's starting point
       CU(cudaMemcpyAsync(s.u, s.nu0, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1331,9 +1406,13 @@ pf_status oramn_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_ste
     phi = phi0;
     if (phi0 <= tol) break;
     double da_prev = HUGE_VAL;
+    if (trace_enabled())
+      fprintf(stderr, "[pf-oramn] outer %d phi0 %.4e tol %.4e oram_its %d\n", outer, phi0, tol,
+              oram_its);
     while (phi / phi0 > o.switch_tol && phi > tol && oram_its < o.am_maxit) {
       double da, durel;
-      TRY(oram_iteration(s, st, o, rep, o.omega, da_prev, &da, &durel));
+      bool sub_ok = true;
+      TRY(oram_iteration(s, st, o, rep, o.omega, da_prev, &da, &durel, &sub_ok));
       da_prev = da;
       ++oram_its;
       if (rep) rep->am_iters = oram_its;
@@ -1486,7 +1565,7 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->precision = PF_FP64;
   o->omega = 1.0;
   o->am_tol = 1e-6;
-  o->am_maxit = 2000;
+  o->am_maxit = 20000;
   o->u_rtol = 1e-8;
   o->inner_rtol = 1e-4;
   o->cg_maxit = 2000;
@@ -1595,6 +1674,7 @@ static pf_status check_opts(const pf_solver_opts* o) {
     return fail(PF_EINVAL, "iteration limits must be positive");
   if (!(o->am_forcing >= 0.0) || !(o->am_forcing_max >= 0.0))
     return fail(PF_EINVAL, "am_forcing and am_forcing_max must be >= 0");
+  if (o->omega_rule != 0 && o->omega_rule != 1) return fail(PF_EINVAL, "omega_rule must be 0 or 1");
   if (o->algo == PF_ALGO_ORAM_N &&
       (o->newton_maxit < 1 || o->minres_maxit < 1 || !(o->switch_tol > 0.0 && o->switch_tol < 1.0) ||
        !(o->newton_rtol > 0.0) || !(o->minres_rtol > 0.0 && o->minres_rtol < 1.0)))
@@ -1621,8 +1701,16 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   pf_step_report r{};
   r.omega_bar_min = o->omega;
   pf_status status = begin_step(*s, st, *L);
+  // ||Phi|| of the full optimality system (eq. kkt) at the start and the end of the step, so
+  // that the residual a converged step leaves is visible (ORAM-N computes both itself)
+  const bool am_algo = o->algo != PF_ALGO_ORAM_N;
+  if (status == PF_OK && am_algo) status = full_residual(*s, st, o->zeta, &r.phi_start);
   if (status == PF_OK)
     status = o->algo == PF_ALGO_ORAM_N ? oramn_step(*s, st, *o, &r) : oram_step(*s, st, *o, &r);
+  if ((status == PF_OK || status == PF_ENOTCONV) && am_algo) {
+    pf_status e1 = full_residual(*s, st, o->zeta, &r.phi_norm);
+    if (e1 != PF_OK) status = e1;
+  }
   if (status == PF_OK || status == PF_ENOTCONV) {
     pf_status e2 = energy_now(*s, st, r.energy);
     if (e2 != PF_OK) status = e2;
@@ -1697,6 +1785,10 @@ pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   const int mode = masked ? M_MASKED : M_APPLY;
+  // the operator reads and writes (u_x, u_y) pairs as one vector access
+  const uintptr_t pair = precision == PF_FP64 ? 16 : 8;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % pair)
+    return fail(PF_EINVAL, "x and y must be aligned to %d bytes", (int)pair);
   if (precision == PF_FP64) {
     ElasticArgs<double> a{};
     a.x = static_cast<const double*>(x);
@@ -1719,6 +1811,7 @@ pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* 
 
 pf_status pf_op_elastic_residual(pf_sim* s, double* r, double* norm2, void* stream) {
   if (!s || !r) return fail(PF_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(r) % 16) return fail(PF_EINVAL, "r must be 16-byte aligned");
   CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));

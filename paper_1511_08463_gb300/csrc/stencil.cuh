@@ -152,6 +152,31 @@ __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
 // ----------------------------------------------------------------------------------------------
 // elasticity operator K(alpha) (2 dofs per node, interleaved)
 // ----------------------------------------------------------------------------------------------
+// (u_x, u_y) of one node as a single 8-byte (float) or 16-byte (double) access; every interleaved
+// vector of the library starts on a 256-byte boundary, and the entry points that take caller
+// vectors check their alignment.
+template <class T>
+struct Pair {
+  T x, y;
+};
+template <class T>
+__device__ __forceinline__ Pair<T> ld_pair(const T* p, int node) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(p + 2 * (size_t)node);
+    return Pair<T>{v.x, v.y};
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p + 2 * (size_t)node);
+    return Pair<T>{v.x, v.y};
+  }
+}
+template <class T>
+__device__ __forceinline__ void st_pair(T* p, int node, T x, T y) {
+  if constexpr (sizeof(T) == 4)
+    *reinterpret_cast<float2*>(p + 2 * (size_t)node) = make_float2(x, y);
+  else
+    *reinterpret_cast<double2*>(p + 2 * (size_t)node) = make_double2(x, y);
+}
+
 // COEF_ALPHA: abar_T from the three nodal damage values; COEF_ELEM: abar_T read per element.
 enum { COEF_ALPHA = 0, COEF_ELEM = 1 };
 
@@ -200,8 +225,12 @@ struct ElasticOp {
 
   __device__ V load(int node, int X2, int Y2) const {
     V v;
-    v.ux = args.x ? args.x[2 * node] : T(0);  // M_CHEB without x: smoothing from zero
-    v.uy = args.x ? args.x[2 * node + 1] : T(0);
+    v.ux = v.uy = T(0);  // M_CHEB without x: smoothing from zero
+    if (args.x) {
+      const Pair<T> u = ld_pair(args.x, node);
+      v.ux = u.x;
+      v.uy = u.y;
+    }
     if (MODE == M_CHEB && args.xc) {
       v.ux += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0);
       v.uy += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 1);
@@ -262,28 +291,25 @@ struct ElasticOp {
     }
     if (MODE == M_APPLY || MODE == M_MASKED) {
       T yx = f0 ? T(0) : fx, yy = f1 ? T(0) : fy;
-      args.y[2 * node] = yx;
-      args.y[2 * node + 1] = yy;
+      st_pair(args.y, node, yx, yy);
       if (DOT) red[0] += own.ux * yx + own.uy * yy;
     } else if (MODE == M_RESB) {
-      T rx = f0 ? T(0) : args.b[2 * node] - fx, ry = f1 ? T(0) : args.b[2 * node + 1] - fy;
-      args.y[2 * node] = rx;
-      args.y[2 * node + 1] = ry;
+      const Pair<T> b = ld_pair(args.b, node);
+      T rx = f0 ? T(0) : b.x - fx, ry = f1 ? T(0) : b.y - fy;
+      st_pair(args.y, node, rx, ry);
       if (DOT) red[0] += rx * rx + ry * ry;
     } else if (MODE == M_RESID) {
       T rx = f0 ? T(0) : -fx, ry = f1 ? T(0) : -fy;
-      args.y[2 * node] = rx;
-      args.y[2 * node + 1] = ry;
+      st_pair(args.y, node, rx, ry);
       red[0] += rx * rx + ry * ry;
     } else if (MODE == M_CHEB) {
-      T rx = args.b[2 * node] - fx, ry = args.b[2 * node + 1] - fy;
-      T px = args.d ? args.d[2 * node] : T(0), py = args.d ? args.d[2 * node + 1] : T(0);
-      T dx = f0 ? T(0) : args.cd * px + args.cr * args.dinv[2 * node] * rx;
-      T dy = f1 ? T(0) : args.cd * py + args.cr * args.dinv[2 * node + 1] * ry;
-      args.dout[2 * node] = dx;
-      args.dout[2 * node + 1] = dy;
-      args.y[2 * node] = own.ux + dx;
-      args.y[2 * node + 1] = own.uy + dy;
+      const Pair<T> b = ld_pair(args.b, node), di = ld_pair(args.dinv, node);
+      const Pair<T> p = args.d ? ld_pair(args.d, node) : Pair<T>{T(0), T(0)};
+      T rx = b.x - fx, ry = b.y - fy;
+      T dx = f0 ? T(0) : args.cd * p.x + args.cr * di.x * rx;
+      T dy = f1 ? T(0) : args.cd * p.y + args.cr * di.y * ry;
+      st_pair(args.dout, node, dx, dy);
+      st_pair(args.y, node, own.ux + dx, own.uy + dy);
     }
   }
 };

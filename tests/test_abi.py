@@ -77,12 +77,12 @@ def test_solver_opts_layout_matches_header(lib):
     assert lib.pf_default_opts(C.cast(raw, C.POINTER(B.pf_solver_opts))) == B.PF_OK
     assert all(b == 0xAB for b in raw[size:])  # nothing written past the binding's struct
     o = B.pf_solver_opts.from_buffer(raw)
-    expect = dict(algo=B.PF_ALGO_ORAM, precision=B.PF_FP64, omega=1.0, am_tol=1e-6, am_maxit=2000,
+    expect = dict(algo=B.PF_ALGO_ORAM, precision=B.PF_FP64, omega=1.0, am_tol=1e-6, am_maxit=20000,
                   u_rtol=1e-8, inner_rtol=1e-4, cg_maxit=2000, rs_rtol=1e-8, rs_maxit=100,
                   alpha_cg_rtol=1e-6, zeta=1e-10, mg_levels_max=0, mg_degree=2, switch_tol=1e-2,
                   newton_rtol=1e-8, newton_maxit=30, minres_maxit=500, minres_rtol=1e-6,
                   use_graphs=1, batch_workers=8, am_forcing=0.0, am_forcing_max=1e-3, mg_tail=1,
-                  mg_coarse_degree=0)
+                  mg_coarse_degree=0, omega_rule=0)
     assert [f for f, _ in B.pf_solver_opts._fields_] == list(expect)
     for k, v in expect.items():
         assert getattr(o, k) == v, k

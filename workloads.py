@@ -22,6 +22,7 @@ from typing import Dict, List, Optional, Tuple
 import numpy as np
 
 EDGES = ("left", "right", "bottom", "top")
+E_DEFAULT, GC_DEFAULT = 1.0, 1.0  # Young's modulus and toughness of every workload
 COMPS = ("ux", "uy", "alpha")
 
 
@@ -59,6 +60,11 @@ class Workload:
     alpha_boxes: List[Tuple[int, int, int, int, float]] = field(default_factory=list)
     loads: List[Tuple[float, float]] = field(default_factory=list)
     omega: float = 1.0
+    # Prescribed displacements that follow a moving Mode-I crack tip (Section 4.1): when set,
+    # dict(KI=stress intensity factor, x_tip0=tip abscissa at t = 0, v=tip speed, y_line=crack
+    # line ordinate); the prescribed value of component c on a fixed edge is then
+    # g * u_bar_c(x - x_tip0 - v t, y - y_line) instead of t * g.
+    mode_I: Optional[Dict[str, float]] = None
 
     @property
     def hx(self) -> float:
@@ -159,6 +165,30 @@ def thermal_shock(nx: int = 1024, ny: int = 256, n_steps: int = 40, ell_over_h: 
         nu=nu, ell=ell, model=model, beta=1.0, pen=pen_over_ell * ell, k_ell=k_ell,
         fixed={"top": {"ux": 0.0, "uy": 0.0}, "left": {"ux": 0.0}, "right": {"ux": 0.0}},
         loads=loads, omega=omega)
+
+
+def surfing(nx: int = 200, ny: int = 100, ell: float = 0.05, n_steps: int = 30,
+            t_max: float = 1.2, model: str = "AT1", kind: str = "crossed", nu: float = 0.3,
+            omega: float = 1.6, k_ell: float = 1e-6, crack_length: float = 0.05,
+            speed: float = 1.0, ki_ratio: float = 1.0) -> Workload:
+    """Surfing (Section 4.1): slab [0, 2] x [-1/2, 1/2], plane stress, the asymptotic Mode-I
+    displacement of eq. (surfingloading) prescribed on the whole boundary with its tip at
+    x = crack_length + speed * t; K_I = ki_ratio * sqrt(Gc E); a pre-existing crack (alpha = 1)
+    on the nodes with x <= crack_length and |y| <= h; loads t_k = k t_max / n_steps."""
+    if ny % 2:
+        raise ValueError("ny must be even (crack line y = 0 on the grid)")
+    lx, ly = 2.0, 1.0
+    hx = lx / nx
+    loads = [(t_max * k / n_steps, 0.0) for k in range(1, n_steps + 1)]
+    x2c = int(round(2 * crack_length / hx))
+    crack = (0, x2c, ny - 2, ny + 2, 1.0)
+    fix = {"ux": 1.0, "uy": 1.0}
+    return Workload(
+        name=f"surfing_{nx}x{ny}_ell{ell:g}", kind=kind, nx=nx, ny=ny, x0=0.0, y0=-0.5, lx=lx,
+        ly=ly, nu=nu, ell=ell, model=model, k_ell=k_ell, plane="stress",
+        fixed={e: dict(fix) for e in EDGES}, alpha_boxes=[crack], loads=loads, omega=omega,
+        mode_I=dict(KI=ki_ratio * math.sqrt(GC_DEFAULT * E_DEFAULT), x_tip0=crack_length,
+                    v=speed, y_line=0.0))
 
 
 def ly_default(nx: int, ny: int) -> float:
