@@ -86,6 +86,9 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=256,
                     help="instances in the batch leg (0: no batch leg)")
     ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--omega-sweep", action="store_true",
+                    help="alternate-minimization iterations versus omega (Tables 1-3) on the "
+                         "surfing, bar and thermal workloads, then exit")
     return ap.parse_args()
 
 
@@ -222,7 +225,7 @@ def cpu_baseline_record(size: int, step_index: int, am_iters_per_step: float):
     it_s, t, p = oracle_iteration_seconds(size, step_index)
     bar = oracle_bar_full_run()
     return {"value": 1.0 / (it_s * am_iters_per_step), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "extrapolated": True,
+            "extrapolated": True, "host_cores": os.cpu_count(),
             "bar_128x16_full_run": {"seconds": bar["seconds"], "load_steps": bar["steps"],
                                     "am_iters": bar["its"],
                                     "load_steps_per_s": bar["steps"] / bar["seconds"]},
@@ -275,7 +278,7 @@ def run_reference(args):
             "config": {"workload": f"notched_square_{args.size}_crossed_AT1_ORAM_omega1.5",
                        "mesh": f"{args.size}x{args.size} crossed P1", "parallelism": "replicas"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "host_cores": os.cpu_count(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -391,6 +394,35 @@ def serve_record(args, ctx):
     }
 
 
+def omega_sweep_record(ctx):
+    """AM iterations and time of whole schedules for fixed omega in 1.0 .. 1.8 and the automated
+    omega, on the three workloads of the paper's over-relaxation tables: surfing (Table 1), the
+    bar (Table 2) and the thermal shock (Table 3), mixed precision, default tolerances."""
+    import workloads as W
+    from paper_1511_08463_gb300 import sim as S
+
+    cases = {"surfing_52x26_ell0.2": W.surfing(nx=52, ny=26, ell=0.2, n_steps=8, t_max=1.2),
+             "bar_128x16": W.bar(),
+             "thermal_128x32": W.thermal_shock(nx=128, ny=32, n_steps=20)}
+    out = {}
+    for name, w in cases.items():
+        rows = {}
+        for om in (1.0, 1.2, 1.4, 1.6, 1.8, "auto"):
+            opts = S.make_opts(omega=1.0 if om == "auto" else om, omega_auto=int(om == "auto"),
+                               precision="mixed", am_maxit=AM_MAXIT)
+            g = S.Sim(w, ctx)
+            its, secs, bad = 0, 0.0, 0
+            for ld in w.loads:
+                r = g.load_step(*ld, opts, allow_notconv=True)
+                its += r["am_iters"]
+                secs += r["seconds"]
+                bad += r["status"] != 0
+            g.close()
+            rows[str(om)] = {"am_iters": its, "seconds": round(secs, 3), "not_ok": bad}
+        out[name] = rows
+    return out
+
+
 def batch_record(args, ctx):
     """Batch leg: seeded notched squares (N log-uniform on [64, 256] in multiples of 16, ell in
     [2h, 8h], nu in [0.2, 0.35]), one load step each from rest to t ~ U[0.5, 1] (before crack
@@ -449,6 +481,11 @@ def run_ours(args):
     from paper_1511_08463_gb300 import sim as S
 
     lib = B.load()
+    if args.omega_sweep:
+        rec = omega_sweep_record(S.Context(local))
+        if rank == 0:
+            print(json.dumps({"omega_sweep": rec}), flush=True)
+        return 0
     if args.serve_only:
         rec = serve_record(args, S.Context(local))
         if rank == 0:

@@ -69,7 +69,15 @@ enum { PF_COMP_UX = 0, PF_COMP_UY = 1, PF_COMP_ALPHA = 2 };
  *   edges meeting at a corner must agree on a component they both prescribe.
  *   pins: single prescribed nodes (doubled units), same value rule.
  * boxes: nodes with box[k][0] <= X2 <= box[k][1] and box[k][2] <= Y2 <= box[k][3] start with
- *   alpha = alpha_prev = box_value[k] (a pre-existing crack when 1). */
+ *   alpha = alpha_prev = box_value[k] (a pre-existing crack when 1).
+ * mode_I != 0: moving-crack boundary data (Section 4.1, eq. surfingloading): the prescribed value
+ *   of displacement component c on a fixed edge or pin is load * u_bar_c(x - x_tip(t), y -
+ *   mode_I_param[3]) with x_tip(t) = mode_I_param[1] + mode_I_param[2] * t, instead of t * load;
+ *   u_bar = K/(2 mu) sqrt(r/(2 pi)) (kappa - cos theta) (cos(theta/2), sin(theta/2)) is the
+ *   asymptotic Mode-I displacement with K = mode_I_param[0], (r, theta) polar around the tip
+ *   (theta in (-pi, pi]), kappa = (3 - nu)/(1 + nu) in plane stress and 3 - 4 nu in plane
+ *   strain, mu and nu from the sim's material.  Node coordinates are x0 + lx X2 / (2 nx),
+ *   y0 + ly Y2 / (2 ny). */
 typedef struct pf_mesh_desc {
   int32_t kind, nx, ny;
   double x0, y0, lx, ly;
@@ -81,6 +89,8 @@ typedef struct pf_mesh_desc {
   int32_t n_boxes;
   int32_t box[PF_MAX_BOXES][4];
   double box_value[PF_MAX_BOXES];
+  int32_t mode_I;
+  double mode_I_param[4];  /* K_I, tip abscissa at t = 0, tip speed, crack-line ordinate */
 } pf_mesh_desc;
 
 /* Material (Section 1.1 and Section 4): Young's modulus E, Poisson ratio nu, toughness Gc,
@@ -148,6 +158,22 @@ typedef struct pf_solver_opts {
                             * recursive midpoint rule of Section 2.1 (omega, (1+omega)/2, ... until
                             * the update stays in the box); 1: always omega, then projection onto
                             * the box [alpha_prev, 1] */
+  int32_t omega_auto;      /* 1: automated omega (no counterpart in the paper, which leaves it
+                            * open in Section 2.2): every 5 iterations of a load step, with rho the
+                            * contraction of max|alpha^k - alpha^{k-1}| over them, mu^2 =
+                            * (rho + omega - 1)^2 / (rho omega^2) and omega <- 2 / (1 + sqrt(1 -
+                            * mu^2)) clamped to [1, omega_max] (the optimum of two-block SOR).
+                            * Each load step starts from `omega`.  0 (default): fixed omega. */
+  double omega_max;        /* upper bound of the automated omega (default 1.9) */
+  int32_t autotune;        /* 1: pf_load_step takes the smoother degrees and FP32 stencil tile
+                            * heights that pf_autotune found for this mesh (kind, nx, ny) and
+                            * precision, running pf_autotune first if none is cached; they replace
+                            * mg_degree, mg_coarse_degree and the two tile heights below.
+                            * 0 (default): as given. */
+  int32_t tile_rows_fine, tile_rows_coarse;  /* stencil tile height (vertex rows per thread
+                            * block of 32 columns) of the FP32 operator kernels on the finest
+                            * level and on the coarser levels: 4, 8 or 16 (0 (default): 8).  Only
+                            * the speed depends on them. */
 } pf_solver_opts;
 
 /* Per-step report (all counts summed over the step).  phi_start / phi_norm: ||Phi||_2 of the
@@ -168,6 +194,7 @@ typedef struct pf_step_report {
                               iteration cap or with a failed line search; the stopping test of
                               the load step is accepted only after an iteration whose two
                               subproblems both converged */
+  double omega_final;      /* relaxation parameter in use at the end of the step */
 } pf_step_report;
 
 typedef struct pf_ctx pf_ctx;
@@ -375,6 +402,26 @@ pf_status pf_op_full_residual(pf_sim* sim, double* phi_norm, void* stream);
  * stream, so it cannot be recorded into a CUDA graph by stream capture. */
 pf_status pf_energy_noalloc(const pf_mesh_desc* d, const pf_material* m, const pf_load* L,
                             const double* u, const double* alpha, double out[3], void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Autotuner (no counterpart in the paper).  Picks, for the sim's mesh and o->precision, the
+ * Chebyshev smoothing steps per level (mg_degree on the finest level, mg_coarse_degree below) and
+ * the stencil tile height of the FP32 operator kernels (4, 8 or 16 rows of 32 vertices per
+ * thread block, one height for the finest level and one for the coarser levels), by timing on
+ * `stream` whole preconditioned-CG solves of the elasticity operator at the sim's current damage
+ * field (right-hand side K(alpha) v with v the resident displacement on the free dofs, or a fixed
+ * pseudo-random field while it is zero; to o->inner_rtol in PF_MIXED, 1e-8 in PF_FP64): the
+ * default first, then the other 11 degree pairs of (1-4) x (1-3) at the default tiles, then the
+ * 8 other tile pairs at the best degrees (PF_MIXED only).  The fastest configuration is kept in a
+ * process-wide cache keyed by (kind, nx, ny, precision) and applied to the sim; the resident
+ * fields are not changed.  out may be NULL.  Synchronous.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct pf_tune_report {
+  int32_t mg_degree, mg_coarse_degree, tile_rows_fine, tile_rows_coarse, trials;
+  int32_t iters_best, iters_default;
+  double ms_best, ms_default;  /* one solve: the chosen and the default configuration */
+} pf_tune_report;
+pf_status pf_autotune(pf_sim* sim, const pf_solver_opts* o, void* stream, pf_tune_report* out);
 
 /* ---------------------------------------------------------------------------------------------
  * Launch accounting and kernel timing (tracing support; process-wide).  Every kernel the

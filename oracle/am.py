@@ -100,9 +100,30 @@ def oram_iteration(prob, omega, dT, zeta=1e-10, qp_rtol=1e-13):
                 qp_status=qinfo["status"])
 
 
+# Automated choice of omega (Section 2.2 conjectures that the best omega minimizes the spectral
+# radius of the SOR iteration matrix and leaves its automation open).  Reading: for a two-block
+# consistently ordered system, an SOR eigenvalue lam and a Jacobi eigenvalue mu satisfy
+# (lam + omega - 1)^2 = lam omega^2 mu^2, and the optimum is omega = 2 / (1 + sqrt(1 - mu^2)).
+OMEGA_PERIOD = 5  # iterations between two estimates
+
+
+def omega_update(rho, omega, omega_max):
+    """New omega from the observed contraction rho at the current omega: mu^2 from the SOR
+    eigenvalue relation, then the optimum, clamped to [1, omega_max]; omega itself if rho carries
+    no estimate (rho outside (0, 1) or mu^2 outside [0, 1))."""
+    if not (0.0 < rho < 1.0):
+        return omega
+    mu2 = (rho + omega - 1.0) ** 2 / (rho * omega * omega)
+    if not (0.0 <= mu2 < 1.0):
+        return omega
+    return min(omega_max, max(1.0, 2.0 / (1.0 + np.sqrt(1.0 - mu2))))
+
+
 def load_step(prob, t, dT=0.0, omega=1.0, tol=1e-6, maxit=2000, zeta=1e-10, qp_rtol=1e-13,
-              record_energy=False):
-    """Algorithm 2 (Algorithm 1 when omega = 1) for one load step."""
+              record_energy=False, omega_auto=False, omega_max=1.9):
+    """Algorithm 2 (Algorithm 1 when omega = 1) for one load step.  omega_auto: every
+    OMEGA_PERIOD iterations omega is replaced by omega_update of the contraction of the damage
+    change over those iterations, rho = (dalpha_k / dalpha_{k-P})^(1/P)."""
     begin_step(prob, t, dT)
     hist = []
     energies = [fe.energy(prob.mat, prob.geo, prob.u, prob.alpha, dT)[2]] if record_energy else []
@@ -110,7 +131,13 @@ def load_step(prob, t, dT=0.0, omega=1.0, tol=1e-6, maxit=2000, zeta=1e-10, qp_r
     k = 0
     for k in range(1, maxit + 1):
         d = oram_iteration(prob, omega, dT, zeta=zeta, qp_rtol=qp_rtol)
+        d["omega"] = omega
         hist.append(d)
+        if omega_auto and k % OMEGA_PERIOD == 0 and k > OMEGA_PERIOD:
+            prev = hist[k - 1 - OMEGA_PERIOD]["dalpha"]
+            if prev > 0.0 and d["dalpha"] > 0.0:
+                omega = omega_update((d["dalpha"] / prev) ** (1.0 / OMEGA_PERIOD), omega,
+                                     omega_max)
         if record_energy:
             energies.append(fe.energy(prob.mat, prob.geo, prob.u, prob.alpha, dT)[2])
         if d["dalpha"] <= tol and d["du_rel"] <= tol:

@@ -27,7 +27,8 @@ class pf_mesh_desc(C.Structure):
                 ("n_pins", C.c_int32), ("pin_x2", C.c_int32 * PF_MAX_PINS),
                 ("pin_y2", C.c_int32 * PF_MAX_PINS), ("pin_comp", C.c_int32 * PF_MAX_PINS),
                 ("pin_load", C.c_double * PF_MAX_PINS), ("n_boxes", C.c_int32),
-                ("box", (C.c_int32 * 4) * PF_MAX_BOXES), ("box_value", C.c_double * PF_MAX_BOXES)]
+                ("box", (C.c_int32 * 4) * PF_MAX_BOXES), ("box_value", C.c_double * PF_MAX_BOXES),
+                ("mode_I", C.c_int32), ("mode_I_param", C.c_double * 4)]
 
 
 class pf_material(C.Structure):
@@ -51,7 +52,10 @@ class pf_solver_opts(C.Structure):
                 ("minres_rtol", C.c_double), ("use_graphs", C.c_int32),
                 ("batch_workers", C.c_int32), ("am_forcing", C.c_double),
                 ("am_forcing_max", C.c_double), ("mg_tail", C.c_int32),
-                ("mg_coarse_degree", C.c_int32), ("omega_rule", C.c_int32)]
+                ("mg_coarse_degree", C.c_int32), ("omega_rule", C.c_int32),
+                ("omega_auto", C.c_int32), ("omega_max", C.c_double),
+                ("autotune", C.c_int32), ("tile_rows_fine", C.c_int32),
+                ("tile_rows_coarse", C.c_int32)]
 
 
 class pf_step_report(C.Structure):
@@ -63,12 +67,22 @@ class pf_step_report(C.Structure):
                 ("omega_bar_min", C.c_double), ("energy", C.c_double * 3),
                 ("seconds", C.c_double), ("u_solves_reused", C.c_int64),
                 ("u_notconv", C.c_int64), ("newton_steepest", C.c_int64),
-                ("alpha_notconv", C.c_int64)]
+                ("alpha_notconv", C.c_int64), ("omega_final", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["energy"] = list(self.energy)
         return d
+
+
+class pf_tune_report(C.Structure):
+    _fields_ = [("mg_degree", C.c_int32), ("mg_coarse_degree", C.c_int32),
+                ("tile_rows_fine", C.c_int32), ("tile_rows_coarse", C.c_int32),
+                ("trials", C.c_int32), ("iters_best", C.c_int32), ("iters_default", C.c_int32),
+                ("ms_best", C.c_double), ("ms_default", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class pf_job(C.Structure):
@@ -120,6 +134,7 @@ _SIGS = {
     "pf_op_alpha_solve": (C.c_int, [_VP, C.POINTER(pf_solver_opts), _VP,
                                     C.POINTER(pf_step_report)]),
     "pf_op_full_residual": (C.c_int, [_VP, C.POINTER(C.c_double), _VP]),
+    "pf_autotune": (C.c_int, [_VP, C.POINTER(pf_solver_opts), _VP, C.POINTER(pf_tune_report)]),
     "pf_energy_noalloc": (C.c_int, [C.POINTER(pf_mesh_desc), C.POINTER(pf_material),
                                     C.POINTER(pf_load), _VP, _VP, C.POINTER(C.c_double), _VP]),
     "pf_server_create": (C.c_int, [_VP, _VP, C.c_size_t, C.c_int, C.POINTER(_VP)]),

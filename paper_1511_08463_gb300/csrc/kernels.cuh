@@ -50,11 +50,19 @@ void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at,
 struct LiftData {
   double load[4][3];
   double pin_load[PF_MAX_PINS];
+  // moving Mode-I crack data (pf_mesh_desc.mode_I): the value is load * u_bar(x - xt0 - v t,
+  // y - yl) with u_bar = K/(2 mu) sqrt(r/(2 pi)) (kappa - cos theta) (cos, sin)(theta/2)
+  int mode_I;
+  double K, xt0, v, yl, mu, kappa;
+  double x0, y0, lx, ly;
 };
 void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld);
 // u <- u on free dofs, masked copy helpers
 template <class T>
 void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp);  // zero prescribed components
+// y_i = a deterministic pseudo-random value in [-1/2, 1/2) from (i, seed) (integer hash)
+template <class T>
+void vec_hash_fill(cudaStream_t s, T* y, size_t n, unsigned seed);
 
 // ---- element-wise kernels -----------------------------------------------------------------------
 template <class T>

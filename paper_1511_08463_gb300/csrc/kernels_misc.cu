@@ -268,6 +268,19 @@ void relax_alpha(cudaStream_t s, const Grid& g, double* alpha, const double* at,
   PF_LAUNCH(kclass(KC_REDUCE, false, false), 0.0, s, pdl_launch(k_relax_alpha, rblocks(g.n), RED_THREADS, 0, s, g, alpha, at, lo, w, alpha32, slot));
 }
 
+// Value of prescribed displacement component c at doubled coordinates (X2, Y2): t * g, or
+// g * u_bar_c for the moving Mode-I crack of Section 4.1 (eq. surfingloading).
+__device__ double lift_value(const Grid& g, const LiftData& ld, int X2, int Y2, int c, double t,
+                             double gload) {
+  if (!ld.mode_I) return t * gload;
+  const double x = ld.x0 + ld.lx * (double)X2 / (2.0 * g.nx);
+  const double y = ld.y0 + ld.ly * (double)Y2 / (2.0 * g.ny);
+  const double dx = x - (ld.xt0 + ld.v * t), dy = y - ld.yl;
+  const double r = hypot(dx, dy), th = atan2(dy, dx);
+  const double amp = ld.K / (2.0 * ld.mu) * sqrt(r / (2.0 * M_PI)) * (ld.kappa - cos(th));
+  return gload * (c == 0 ? amp * cos(0.5 * th) : amp * sin(0.5 * th));
+}
+
 __global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
   pdl_enter();
   int node = blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,10 +288,10 @@ __global__ void k_lift(Grid g, double* u, double t, LiftData ld) {
   int X2, Y2;
   node_coords(g, node, X2, Y2);
   for (int c = 0; c < 2; ++c) {
-    if (X2 == 0 && g.fixed[0][c]) u[2 * node + c] = t * ld.load[0][c];
-    if (X2 == 2 * g.nx && g.fixed[1][c]) u[2 * node + c] = t * ld.load[1][c];
-    if (Y2 == 0 && g.fixed[2][c]) u[2 * node + c] = t * ld.load[2][c];
-    if (Y2 == 2 * g.ny && g.fixed[3][c]) u[2 * node + c] = t * ld.load[3][c];
+    if (X2 == 0 && g.fixed[0][c]) u[2 * node + c] = lift_value(g, ld, X2, Y2, c, t, ld.load[0][c]);
+    if (X2 == 2 * g.nx && g.fixed[1][c]) u[2 * node + c] = lift_value(g, ld, X2, Y2, c, t, ld.load[1][c]);
+    if (Y2 == 0 && g.fixed[2][c]) u[2 * node + c] = lift_value(g, ld, X2, Y2, c, t, ld.load[2][c]);
+    if (Y2 == 2 * g.ny && g.fixed[3][c]) u[2 * node + c] = lift_value(g, ld, X2, Y2, c, t, ld.load[3][c]);
   }
 }
 __global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
@@ -288,7 +301,7 @@ __global__ void k_lift_pins(Grid g, double* u, double t, LiftData ld) {
     int X2 = g.pin_x2[k], Y2 = g.pin_y2[k], node;
     if ((X2 & 1) == 0) node = (Y2 / 2) * (g.nx + 1) + X2 / 2;
     else node = g.nv + (Y2 / 2) * g.nx + X2 / 2;
-    u[2 * node + g.pin_comp[k]] = t * ld.pin_load[k];
+    u[2 * node + g.pin_comp[k]] = lift_value(g, ld, X2, Y2, g.pin_comp[k], t, ld.pin_load[k]);
   }
 }
 void lift_u(cudaStream_t s, const Grid& g, double* u, double t, const LiftData& ld) {
@@ -316,6 +329,28 @@ void mask_fixed(cudaStream_t s, const Grid& g, T* v, int ncomp) {
 }
 template void mask_fixed<double>(cudaStream_t, const Grid&, double*, int);
 template void mask_fixed<float>(cudaStream_t, const Grid&, float*, int);
+
+// integer hash (a xorshift-multiply mix) of the index and a seed, scaled to [-1/2, 1/2)
+template <class T>
+__global__ void k_hash_fill(T* y, size_t n, unsigned seed) {
+  pdl_enter();
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ seed;
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  y[i] = T(double(h) * (1.0 / 4294967296.0) - 0.5);
+}
+template <class T>
+void vec_hash_fill(cudaStream_t s, T* y, size_t n, unsigned seed) {
+  PF_LAUNCH(kclass(KC_VECTOR, sizeof(T) == 8, 0), double(n) * sizeof(T), s,
+            pdl_launch(k_hash_fill<T>, nblocks(n), RED_THREADS, 0, s, y, n, seed));
+}
+template void vec_hash_fill<double>(cudaStream_t, double*, size_t, unsigned);
+template void vec_hash_fill<float>(cudaStream_t, float*, size_t, unsigned);
 
 // ---------------------------------------------------------------------------------------------
 // element-wise kernels: one thread per cell

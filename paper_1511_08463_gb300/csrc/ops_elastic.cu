@@ -20,11 +20,21 @@ static double elastic_bytes(const Grid& g, int coef, int mode, const ElasticArgs
   return double(g.n) * node + coefb;
 }
 
+template <class Op, int TYV>
+static void launch_tile(cudaStream_t s, const Op& op, int id, double bytes) {
+  dim3 block(TX, TYV);
+  dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TYV - 1) / TYV);
+  PF_LAUNCH(id, bytes, s, pdl_launch(stencil_kernel<Op, TYV>, grid, block, 0, s, op));
+}
+// FP32 operators run with the level's tile height (TY_MIN, TY or 16 rows, Grid::tile_rows);
+// FP64 operators always with TY
 template <class Op>
 static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
-  dim3 block(TX, TY);
-  dim3 grid((op.g.nx + 1 + TX - 1) / TX, (op.g.ny + 1 + TY - 1) / TY);
-  PF_LAUNCH(id, bytes, s, pdl_launch(stencil_kernel<Op>, grid, block, 0, s, op));
+  if constexpr (sizeof(typename Op::Scalar) == 4) {
+    if (op.g.tile_rows == TY_MIN) return launch_tile<Op, TY_MIN>(s, op, id, bytes);
+    if (op.g.tile_rows == 16) return launch_tile<Op, 16>(s, op, id, bytes);
+  }
+  launch_tile<Op, TY>(s, op, id, bytes);
 }
 
 template <class T, int K, int C, int M, bool E, bool D>

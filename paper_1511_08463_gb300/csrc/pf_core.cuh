@@ -49,7 +49,9 @@ inline void pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
 constexpr int RIGHT = 0;
 constexpr int CROSSED = 1;
 constexpr int TX = 32;  // stencil tile: vertices per block in x
-constexpr int TY = 8;   // stencil tile: vertices per block in y
+constexpr int TY = 8;   // stencil tile: vertices per block in y (default; FP32 multigrid kernels
+                        // also come with TY_MIN and 16 rows, chosen per level by the autotuner)
+constexpr int TY_MIN = 4;
 constexpr int RED_THREADS = 256;
 constexpr int MAX_RED_BLOCKS = 4096;
 
@@ -89,6 +91,7 @@ struct Grid {
   int npins;
   int pin_x2[PF_MAX_PINS], pin_y2[PF_MAX_PINS], pin_comp[PF_MAX_PINS];
   int interior_pins;  // 1 if some pin lies strictly inside the rectangle
+  int tile_rows;      // stencil tile height of the FP32 kernels on this level (0: TY)
 };
 
 // Material constants in the form the kernels use.

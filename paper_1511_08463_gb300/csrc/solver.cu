@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <type_traits>
 #include <new>
@@ -144,6 +146,11 @@ pf_status validate(const pf_mesh_desc* d) {
     return fail(PF_EINVAL, "mesh %d x %d has too many nodes", d->nx, d->ny);
   if (d->n_pins < 0 || d->n_pins > PF_MAX_PINS) return fail(PF_EINVAL, "bad pin count");
   if (d->n_boxes < 0 || d->n_boxes > PF_MAX_BOXES) return fail(PF_EINVAL, "bad box count");
+  if (d->mode_I != 0 && d->mode_I != 1) return fail(PF_EINVAL, "mode_I must be 0 or 1");
+  if (d->mode_I && !(d->mode_I_param[0] == d->mode_I_param[0] && d->mode_I_param[1] ==
+                     d->mode_I_param[1] && d->mode_I_param[2] == d->mode_I_param[2] &&
+                     d->mode_I_param[3] == d->mode_I_param[3]))
+    return fail(PF_EINVAL, "mode_I parameters must be finite numbers");
   for (int k = 0; k < d->n_pins; ++k) {
     int X2 = d->pin_x2[k], Y2 = d->pin_y2[k];
     bool vert = !(X2 & 1) && !(Y2 & 1), cen = (X2 & 1) && (Y2 & 1);
@@ -259,7 +266,7 @@ void layout(pf_sim& s, Arena& a) {
     take_level<float>(a, s.lv[l], l == L - 1);
     if (l > 0) s.lv[l].exclD = a.take<uint8_t>(s.lv[l].g.n);
   }
-  size_t nb = ((size_t)(g.nx + 1 + TX - 1) / TX) * ((g.ny + 1 + TY - 1) / TY);
+  size_t nb = ((size_t)(g.nx + 1 + TX - 1) / TX) * ((g.ny + 1 + TY_MIN - 1) / TY_MIN);
   nb = std::max<size_t>(nb, MAX_RED_BLOCKS);
   s.part = a.take<double>(nb * 4);
   s.ticket = a.take<unsigned>(64);
@@ -688,7 +695,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   const int pi = sizeof(T) == 8 ? 1 : 0;
   const int degkey = deg * 1000 + s.cdeg;
   if (s.cg_exec[phys][pi] && s.cg_deg[phys][pi] == degkey && s.cg_nl[phys][pi] == s.nl_active &&
-      s.cg_tail[phys][pi] == (int)s.use_tail)
+      s.cg_tail[phys][pi] == (int)s.use_tail && s.cg_tiles[phys][pi] == s.tile_fine * 100 + s.tile_coarse)
     return PF_OK;
   if (s.cg_exec[phys][pi]) {
     cudaGraphExecDestroy(s.cg_exec[phys][pi]);
@@ -751,6 +758,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   s.cg_deg[phys][pi] = degkey;
   s.cg_nl[phys][pi] = s.nl_active;
   s.cg_tail[phys][pi] = (int)s.use_tail;
+  s.cg_tiles[phys][pi] = s.tile_fine * 100 + s.tile_coarse;
   return PF_OK;
 }
 
@@ -804,6 +812,9 @@ pf_status set_load(pf_sim& s, double t, double dT, cudaStream_t st) {
   s.t = t;
   s.dT = dT;
   const Grid& g = s.lv[0].g;
+  s.lift.mu = s.m.mu;  // material constants of the Mode-I boundary field
+  s.lift.kappa = s.mat_in.plane == PF_PLANE_STRESS ? (3.0 - s.mat_in.nu) / (1.0 + s.mat_in.nu)
+                                                   : 3.0 - 4.0 * s.mat_in.nu;
   lift_u(st, g, s.u, t, s.lift);
   s.thermal = s.m.model && s.mat_in.beta != 0.0 && dT != 0.0;
   if (s.thermal) {
@@ -1108,13 +1119,33 @@ pf_status oram_iteration(pf_sim& s, cudaStream_t st, const pf_solver_opts& oin,
   return PF_OK;
 }
 
+// Automated omega: the optimum of two-block SOR, 2 / (1 + sqrt(1 - mu^2)), with the Jacobi
+// eigenvalue mu^2 recovered from the contraction rho observed at the current omega through
+// (rho + omega - 1)^2 = rho omega^2 mu^2; clamped to [1, omega_max].
+constexpr int OMEGA_PERIOD = 5;
+double omega_update(double rho, double omega, double omega_max) {
+  if (!(rho > 0.0 && rho < 1.0)) return omega;
+  const double mu2 = (rho + omega - 1.0) * (rho + omega - 1.0) / (rho * omega * omega);
+  if (!(mu2 >= 0.0 && mu2 < 1.0)) return omega;
+  return std::min(omega_max, std::max(1.0, 2.0 / (1.0 + sqrt(1.0 - mu2))));
+}
+
 pf_status oram_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_report* rep) {
-  const double omega = o.algo == PF_ALGO_AM ? 1.0 : o.omega;
+  double omega = o.algo == PF_ALGO_AM ? 1.0 : o.omega;
+  const bool adapt = o.omega_auto && o.algo != PF_ALGO_AM;
   double da_prev = HUGE_VAL;
+  double da_hist[OMEGA_PERIOD + 1] = {};  // da of iterations k - OMEGA_PERIOD .. k (ring)
   for (int k = 1; k <= o.am_maxit; ++k) {
     double da, durel;
     bool sub_ok = true;
     TRY(oram_iteration(s, st, o, rep, omega, da_prev, &da, &durel, &sub_ok));
+    if (rep) rep->omega_final = omega;
+    da_hist[k % (OMEGA_PERIOD + 1)] = da;
+    if (adapt && k % OMEGA_PERIOD == 0 && k > OMEGA_PERIOD) {
+      const double prev = da_hist[(k - OMEGA_PERIOD) % (OMEGA_PERIOD + 1)];
+      if (prev > 0.0 && da > 0.0) omega = omega_update(pow(da / prev, 1.0 / OMEGA_PERIOD), omega,
+                                                       o.omega_max);
+    }
     // with inexact solves a small change may only mean a loose solve did not move the state:
     // the test counts only for an iteration run at (nearly) the exact tolerances, i.e. one
     // whose predecessor already met the damage-change criterion
@@ -1428,6 +1459,180 @@ pf_status oramn_step(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_ste
   return phi <= tol ? PF_OK : PF_ENOTCONV;
 }
 
+// ---------------------------------------------------------------------------------------------
+// autotuner: smoother degrees and FP32 stencil tile heights, timed on whole PCG solves
+// ---------------------------------------------------------------------------------------------
+struct TuneCfg {
+  int deg, cdeg, tf, tc;
+};
+struct TuneKey {
+  int kind, nx, ny, prec;
+  bool operator<(const TuneKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (nx != o.nx) return nx < o.nx;
+    if (ny != o.ny) return ny < o.ny;
+    return prec < o.prec;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneCfg> g_tune;
+
+TuneKey tune_key(const pf_sim& s, int precision) {
+  return TuneKey{s.desc.kind, s.desc.nx, s.desc.ny, precision};
+}
+
+// stencil tile heights of the sim's levels: tile_fine on level 0, tile_coarse below
+void apply_tiles(pf_sim& s) {
+  for (size_t l = 0; l < s.lv.size(); ++l) s.lv[l].g.tile_rows = l == 0 ? s.tile_fine : s.tile_coarse;
+}
+
+// the per-call solver settings that pf_load_step derives from the options
+void apply_opts(pf_sim& s, const pf_solver_opts& o) {
+  s.use_graphs = o.use_graphs != 0;
+  s.nl_active = o.mg_levels_max > 0 ? std::min<int>(o.mg_levels_max, (int)s.lv.size())
+                                    : (int)s.lv.size();
+  s.use_tail = o.mg_tail != 0;
+  s.cdeg = o.mg_coarse_degree > 0 ? o.mg_coarse_degree : o.mg_degree;
+}
+
+// mean time of two PCG solves of K(alpha) x = b under configuration c (after one untimed solve
+// that also captures the solve's graph)
+template <class T>
+pf_status time_pcg(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, const TuneCfg& c,
+                   const T* b, double rtol, double* ms, int* its) {
+  s.cdeg = c.cdeg;
+  s.tile_fine = c.tf;
+  s.tile_coarse = c.tc;
+  apply_tiles(s);
+  int64_t it0 = 0, it1 = 0;
+  pf_status e = pcg<T>(s, st, ELASTIC, b, o.cg_maxit, rtol, c.deg, &it0, nullptr);
+  if (e != PF_OK && e != PF_ENOTCONV) return e;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(PF_ECUDA, "cudaEventCreate failed");
+  }
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < 2 && (e == PF_OK || e == PF_ENOTCONV); ++r)
+    e = pcg<T>(s, st, ELASTIC, b, o.cg_maxit, rtol, c.deg, &it1, nullptr);
+  cudaEventRecord(e1, st);
+  cudaError_t se = cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (se != cudaSuccess) return fail(PF_ECUDA, "tuning solve: %s", cudaGetErrorString(se));
+  if (e != PF_OK && e != PF_ENOTCONV) return e;
+  // a configuration whose solve does not converge is never chosen
+  *ms = e == PF_OK ? 0.5 * t : HUGE_VAL;
+  *its = (int)(it1 / 2);
+  return PF_OK;
+}
+
+template <class T>
+pf_status tune_t(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, TuneCfg* best,
+                 pf_tune_report* rep) {
+  const Grid& g = s.lv[0].g;
+  const size_t n2 = 2 * (size_t)g.n;
+  const bool mixed = std::is_same<T, float>::value;
+  setup_elastic<T>(s, st);
+  (mixed ? s.elastic_ready32 : s.elastic_ready64) = true;
+  T *v, *b;
+  if constexpr (std::is_same<T, float>::value) {
+    v = s.nv[0];
+    b = s.tmp32;
+  } else {
+    v = s.tmpb;
+    b = s.tmpa;
+  }
+  // solution of the test solve: the resident displacement (smooth, with the crack's jump) on
+  // the free dofs, like the corrections the u-subproblems compute; a pseudo-random field if the
+  // displacement is still zero
+  vec_convert<T, double>(st, v, s.u, n2);
+  mask_fixed<T>(st, g, v, 2);
+  vec_dot<T>(st, v, v, n2, slot(s, S_TMP));
+  double vv;
+  TRY(read_scalars(s, st, S_TMP, 1, &vv));
+  if (!(vv > 0.0)) {
+    vec_hash_fill<T>(st, v, n2, 12345u);
+    mask_fixed<T>(st, g, v, 2);
+  }
+  apply_op<T>(s, st, ELASTIC, 0, v, b, false, S_TMP);
+  const double rtol = mixed ? o.inner_rtol : 1e-8;
+  const TuneCfg dflt{o.mg_degree, o.mg_coarse_degree > 0 ? o.mg_coarse_degree : o.mg_degree, 0, 0};
+  double ms_d;
+  int it_d;
+  TRY(time_pcg<T>(s, st, o, dflt, b, rtol, &ms_d, &it_d));
+  TuneCfg cur = dflt;
+  double ms_b = ms_d;
+  int it_b = it_d, trials = 1;
+  for (int d = 1; d <= 4; ++d)
+    for (int cd = 1; cd <= 3; ++cd) {
+      const TuneCfg c{d, cd, 0, 0};
+      if (c.deg == dflt.deg && c.cdeg == dflt.cdeg) continue;
+      double ms;
+      int it;
+      TRY(time_pcg<T>(s, st, o, c, b, rtol, &ms, &it));
+      ++trials;
+      if (ms < ms_b) {
+        ms_b = ms;
+        it_b = it;
+        cur = c;
+      }
+    }
+  if (mixed) {
+    const int rows[3] = {TY_MIN, TY, 16};
+    const TuneCfg base = cur;
+    for (int a = 0; a < 3; ++a)
+      for (int c2 = 0; c2 < 3; ++c2) {
+        const TuneCfg c{base.deg, base.cdeg, rows[a] == TY ? 0 : rows[a], rows[c2] == TY ? 0 : rows[c2]};
+        if (c.tf == 0 && c.tc == 0) continue;
+        double ms;
+        int it;
+        TRY(time_pcg<T>(s, st, o, c, b, rtol, &ms, &it));
+        ++trials;
+        if (ms < ms_b) {
+          ms_b = ms;
+          it_b = it;
+          cur = c;
+        }
+      }
+  }
+  *best = cur;
+  if (rep) {
+    rep->mg_degree = cur.deg;
+    rep->mg_coarse_degree = cur.cdeg;
+    rep->tile_rows_fine = cur.tf ? cur.tf : TY;
+    rep->tile_rows_coarse = cur.tc ? cur.tc : TY;
+    rep->trials = trials;
+    rep->iters_best = it_b;
+    rep->iters_default = it_d;
+    rep->ms_best = ms_b;
+    rep->ms_default = ms_d;
+  }
+  s.xu_valid = false;
+  return PF_OK;
+}
+
+// tune, cache and apply (the sim's options must already be applied by apply_opts)
+pf_status tune_sim(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, TuneCfg* out,
+                   pf_tune_report* rep) {
+  TuneCfg c;
+  if (o.precision == PF_MIXED) TRY(tune_t<float>(s, st, o, &c, rep));
+  else TRY(tune_t<double>(s, st, o, &c, rep));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(s, o.precision)] = c;
+  }
+  s.cdeg = c.cdeg;
+  s.tile_fine = c.tf;
+  s.tile_coarse = c.tc;
+  apply_tiles(s);
+  *out = c;
+  return PF_OK;
+}
+
 }  // namespace
 
 namespace pf {
@@ -1496,6 +1701,15 @@ pf_status create_sim(pf_ctx* ctx, const pf_mesh_desc* d, void* ws, size_t ws_byt
   for (int e = 0; e < 4; ++e)
     for (int c = 0; c < 3; ++c) s->lift.load[e][c] = d->load[e][c];
   for (int k = 0; k < d->n_pins; ++k) s->lift.pin_load[k] = d->pin_load[k];
+  s->lift.mode_I = d->mode_I;
+  s->lift.K = d->mode_I_param[0];
+  s->lift.xt0 = d->mode_I_param[1];
+  s->lift.v = d->mode_I_param[2];
+  s->lift.yl = d->mode_I_param[3];
+  s->lift.x0 = d->x0;
+  s->lift.y0 = d->y0;
+  s->lift.lx = d->lx;
+  s->lift.ly = d->ly;
   // initial state on the host: u = 0, alpha = alpha_prev from the damage boxes and the damage
   // Dirichlet data
   const Grid& g = s->lv[0].g;
@@ -1586,6 +1800,11 @@ pf_status pf_default_opts(pf_solver_opts* o) {
   o->am_forcing_max = 1e-3;
   o->mg_tail = 1;
   o->mg_coarse_degree = 0;
+  o->omega_rule = 0;
+  o->omega_auto = 0;
+  o->omega_max = 1.9;
+  o->autotune = 0;
+  o->tile_rows_fine = o->tile_rows_coarse = 0;
   return PF_OK;
 }
 
@@ -1675,6 +1894,13 @@ static pf_status check_opts(const pf_solver_opts* o) {
   if (!(o->am_forcing >= 0.0) || !(o->am_forcing_max >= 0.0))
     return fail(PF_EINVAL, "am_forcing and am_forcing_max must be >= 0");
   if (o->omega_rule != 0 && o->omega_rule != 1) return fail(PF_EINVAL, "omega_rule must be 0 or 1");
+  if (o->omega_auto != 0 && o->omega_auto != 1) return fail(PF_EINVAL, "omega_auto must be 0 or 1");
+  if (o->autotune != 0 && o->autotune != 1) return fail(PF_EINVAL, "autotune must be 0 or 1");
+  for (int tr : {o->tile_rows_fine, o->tile_rows_coarse})
+    if (tr != 0 && tr != TY_MIN && tr != TY && tr != 16)
+      return fail(PF_EINVAL, "tile heights must be 0, 4, 8 or 16");
+  if (o->omega_auto && !(o->omega_max >= 1.0 && o->omega_max < 2.0))
+    return fail(PF_EINVAL, "omega_max must lie in [1, 2)");
   if (o->algo == PF_ALGO_ORAM_N &&
       (o->newton_maxit < 1 || o->minres_maxit < 1 || !(o->switch_tol > 0.0 && o->switch_tol < 1.0) ||
        !(o->newton_rtol > 0.0) || !(o->minres_rtol > 0.0 && o->minres_rtol < 1.0)))
@@ -1693,13 +1919,33 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   if (cudaError_t e = cudaSetDevice(s->ctx->device); e != cudaSuccess)
     return fail(PF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
   auto t0 = std::chrono::steady_clock::now();
-  s->use_graphs = o->use_graphs != 0;
-  s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
-                                      : (int)s->lv.size();
-  s->use_tail = o->mg_tail != 0;
-  s->cdeg = o->mg_coarse_degree > 0 ? o->mg_coarse_degree : o->mg_degree;
+  pf_solver_opts oo = *o;
+  apply_opts(*s, oo);
+  s->tile_fine = o->tile_rows_fine == TY ? 0 : o->tile_rows_fine;
+  s->tile_coarse = o->tile_rows_coarse == TY ? 0 : o->tile_rows_coarse;
+  if (o->autotune) {  // the cached configuration for this mesh and precision, tuned on first use
+    TuneCfg c;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(tune_key(*s, o->precision));
+      if (it != g_tune.end()) {
+        c = it->second;
+        have = true;
+      }
+    }
+    if (!have) TRY(tune_sim(*s, st, oo, &c, nullptr));
+    oo.mg_degree = c.deg;
+    oo.mg_coarse_degree = c.cdeg;
+    apply_opts(*s, oo);
+    s->tile_fine = c.tf;
+    s->tile_coarse = c.tc;
+  }
+  apply_tiles(*s);
+  o = &oo;
   pf_step_report r{};
   r.omega_bar_min = o->omega;
+  r.omega_final = o->algo == PF_ALGO_AM ? 1.0 : o->omega;
   pf_status status = begin_step(*s, st, *L);
   // ||Phi|| of the full optimality system (eq. kkt) at the start and the end of the step, so
   // that the residual a converged step leaves is visible (ORAM-N computes both itself)
@@ -1719,6 +1965,21 @@ pf_status pf_load_step(pf_sim* s, const pf_load* L, const pf_solver_opts* o, voi
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rep) *rep = r;
   return status;
+}
+
+pf_status pf_autotune(pf_sim* s, const pf_solver_opts* o, void* stream, pf_tune_report* out) {
+  if (!s) return fail(PF_EINVAL, "null sim");
+  TRY(check_opts(o));
+  if (!s->have_material) return fail(PF_EINVAL, "material not set");
+  CLAIM(s);
+  CU(cudaSetDevice(s->ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  apply_opts(*s, *o);
+  TuneCfg c;
+  pf_tune_report r{};
+  TRY(tune_sim(*s, st, *o, &c, &r));
+  if (out) *out = r;
+  return PF_OK;
 }
 
 pf_status pf_energy(pf_sim* s, void* stream, double out[3]) {

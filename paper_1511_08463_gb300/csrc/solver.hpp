@@ -136,6 +136,8 @@ struct pf_sim {
   int cdeg = 2;  // Chebyshev steps per smoothing on levels >= 1 (pf_solver_opts.mg_coarse_degree)
   int tail_first[2] = {-2, -2};
   int cg_tail[2][2] = {};
+  int cg_tiles[2][2] = {};  // tile configuration the graph was captured with
+  int tile_fine = 0, tile_coarse = 0;  // FP32 stencil tile heights (0: default)
   double* host = nullptr;  // pinned read-back slot from the context's pool
   ~pf_sim() {
     if (host && ctx) ctx->give_slot(host);

@@ -44,8 +44,8 @@ inline Consts<T> make_consts(const Grid& g, const Mat& m) {
 // ----------------------------------------------------------------------------------------------
 // generic tile kernel
 // ----------------------------------------------------------------------------------------------
-template <class Op>
-__global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
+template <class Op, int TYV = TY>
+__global__ void __launch_bounds__(TX* TYV) stencil_kernel(Op op) {
   pdl_enter();
   using V = typename Op::V;
   using R = typename Op::R;
@@ -53,25 +53,25 @@ __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
   constexpr int KIND = Op::KIND;
   constexpr int NE = elems_per_cell(KIND);
   constexpr int NRC = Op::NRC;
-  constexpr int NC = KIND == CROSSED ? TY + 1 : 1;
-  __shared__ V sv[TY + 2][TX + 2];
+  constexpr int NC = KIND == CROSSED ? TYV + 1 : 1;
+  __shared__ V sv[TYV + 2][TX + 2];
   __shared__ V sc[NC][TX + 1];
   // element records stored component-major: consecutive cells -> consecutive words, so both the
   // record writes and the gathers are free of shared-memory bank conflicts
-  __shared__ ET se[NRC][NE][TY + 1][TX + 1];
+  __shared__ ET se[NRC][NE][TYV + 1][TX + 1];
   const Grid& g = op.g;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TYV;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + ty * TX;
 
-  for (int s = tid; s < (TX + 2) * (TY + 2); s += TX * TY) {
+  for (int s = tid; s < (TX + 2) * (TYV + 2); s += TX * TYV) {
     int li = s % (TX + 2), lj = s / (TX + 2);
     int gi = i0 - 1 + li, gj = j0 - 1 + lj;
     bool in = gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny;
     sv[lj][li] = in ? op.load(gj * (g.nx + 1) + gi, 2 * gi, 2 * gj) : Op::zero();
   }
   if constexpr (KIND == CROSSED) {
-    for (int s = tid; s < (TX + 1) * (TY + 1); s += TX * TY) {
+    for (int s = tid; s < (TX + 1) * (TYV + 1); s += TX * TYV) {
       int li = s % (TX + 1), lj = s / (TX + 1);
       int gi = i0 - 1 + li, gj = j0 - 1 + lj;
       bool in = gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(TX* TY) stencil_kernel(Op op) {
 #pragma unroll
     for (int c = 0; c < NRC; ++c) se[c][t][lj][li] = r.c[c];
   };
-  for (int s = tid; s < (TX + 1) * (TY + 1); s += TX * TY) {
+  for (int s = tid; s < (TX + 1) * (TYV + 1); s += TX * TYV) {
     int li = s % (TX + 1), lj = s / (TX + 1);
     int ci = i0 - 1 + li, cj = j0 - 1 + lj;
     bool valid = ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny;
@@ -200,6 +200,7 @@ struct ElasticArgs {
 
 template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT>
 struct ElasticOp {
+  using Scalar = T;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
   static constexpr bool RED_MAX = false;
@@ -341,6 +342,7 @@ struct DamageArgs {
 
 template <class T, int KIND_, int MODE, bool DOT>
 struct DamageOp {
+  using Scalar = T;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
   static constexpr bool RED_MAX = false;
@@ -471,6 +473,7 @@ struct CouplingArgs {
 
 template <class T, int KIND_, bool TRANSPOSE>
 struct CouplingOp {
+  using Scalar = T;
   static constexpr int KIND = KIND_;
   static constexpr int NR = 0;
   static constexpr bool RED_MAX = false;

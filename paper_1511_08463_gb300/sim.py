@@ -31,6 +31,11 @@ def mesh_desc(w) -> B.pf_mesh_desc:
     for k, (xl, xh, yl, yh, v) in enumerate(w.alpha_boxes):
         d.box[k][0], d.box[k][1], d.box[k][2], d.box[k][3] = xl, xh, yl, yh
         d.box_value[k] = v
+    if w.mode_I is not None:
+        d.mode_I = 1
+        m = w.mode_I
+        d.mode_I_param[0], d.mode_I_param[1] = m["KI"], m["x_tip0"]
+        d.mode_I_param[2], d.mode_I_param[3] = m["v"], m["y_line"]
     return d
 
 
@@ -156,6 +161,12 @@ class Sim:
         aa, ap_ = p(alpha, (self.n_nodes,))
         pa, pp = p(alpha_prev, (self.n_nodes,))
         B.check(self.lib.pf_set_fields(self.h, up, ap_, pp))
+
+    def autotune(self, opts=None, stream=None) -> dict:
+        o = opts or make_opts(omega=self.w.omega)
+        r = B.pf_tune_report()
+        B.check(self.lib.pf_autotune(self.h, C.byref(o), C.c_void_p(_stream(stream)), C.byref(r)))
+        return r.as_dict()
 
     def set_load(self, t: float, dT: float = 0.0):
         L = B.pf_load(t, dT)

@@ -82,7 +82,8 @@ def test_solver_opts_layout_matches_header(lib):
                   alpha_cg_rtol=1e-6, zeta=1e-10, mg_levels_max=0, mg_degree=2, switch_tol=1e-2,
                   newton_rtol=1e-8, newton_maxit=30, minres_maxit=500, minres_rtol=1e-6,
                   use_graphs=1, batch_workers=8, am_forcing=0.0, am_forcing_max=1e-3, mg_tail=1,
-                  mg_coarse_degree=0, omega_rule=0)
+                  mg_coarse_degree=0, omega_rule=0, omega_auto=0, omega_max=1.9, autotune=0,
+                  tile_rows_fine=0, tile_rows_coarse=0)
     assert [f for f, _ in B.pf_solver_opts._fields_] == list(expect)
     for k, v in expect.items():
         assert getattr(o, k) == v, k

@@ -171,3 +171,61 @@ def test_dirichlet_lift_sets_prescribed_values_exactly():
     np.testing.assert_array_equal(after[p.u_fixed], t * p.u_load[p.u_fixed])
     np.testing.assert_array_equal(after[~p.u_fixed], before[~p.u_fixed])
     assert np.any(p.u_load[p.u_fixed] != 0)  # the bar's end displacement is a genuine load
+
+
+def test_surfing_dissipation_rate_is_griffith():
+    """Surfing (Section 4.1): with K_I = sqrt(Gc E) the crack runs at the tip speed v, so the
+    surface energy grows at Gc v (Griffith).  AT1 with h = ell/5 overestimates the surface
+    energy of a developed band by a few percent; the rate must be within 10% of Gc v."""
+    w = W.surfing(nx=52, ny=26, ell=0.2, n_steps=8, t_max=1.2)
+    p = Problem(w)
+    es, ts = [], []
+    for (t, dT) in w.loads:
+        r = am.load_step(p, t, dT, omega=w.omega, tol=1e-6)
+        assert r["status"] == "converged"
+        es.append(r["energy"][1])
+        ts.append(t)
+        assert np.all(p.alpha >= p.alpha_prev) and p.alpha.max() <= 1.0
+    rate = (es[-1] - es[3]) / (ts[-1] - ts[3])  # after the start-up transient (t >= 0.6)
+    assert abs(rate - w.Gc * w.mode_I["v"]) <= 0.1 * w.Gc * w.mode_I["v"], rate
+    # the damage band lies on the crack line y = 0 ahead of the initial crack
+    band = (np.abs(p.mesh.xy[:, 1]) < 1e-12) & (p.mesh.xy[:, 0] > 0.3) & (p.mesh.xy[:, 0] < 1.0)
+    assert p.alpha[band].min() > 0.9
+
+
+def test_omega_update_closed_forms():
+    """The automated omega rule against the SOR theory it is read from (two-block consistently
+    ordered case): at omega = 1 the contraction is mu^2, and the update returns the optimum
+    2/(1 + sqrt(1 - mu^2)); at omega above the optimum the SOR eigenvalues have modulus
+    omega - 1, and the update leaves omega unchanged; out-of-range input keeps omega."""
+    for mu2 in (0.5, 0.9, 0.99):
+        opt = 2.0 / (1.0 + np.sqrt(1.0 - mu2))
+        assert abs(am.omega_update(mu2, 1.0, 1.99) - opt) < 1e-12
+        # at the optimum itself the contraction is omega_opt - 1: fixed point
+        assert abs(am.omega_update(opt - 1.0, opt, 1.99) - opt) < 1e-12
+    assert am.omega_update(0.9, 1.0, 1.3) == 1.3  # clamped
+    assert am.omega_update(1.2, 1.4, 1.9) == 1.4 and am.omega_update(0.0, 1.4, 1.9) == 1.4
+
+
+def test_omega_update_on_a_linear_two_block_system():
+    """Block Gauss-Seidel on a random SPD two-block system: the contraction observed at omega = 1
+    fed to the rule gives the omega that minimizes the spectral radius of the block SOR matrix
+    (checked against a dense scan of omega)."""
+    rng = np.random.default_rng(4)
+    n = 6
+    B = rng.normal(size=(n, n))
+    B *= 0.95 / np.linalg.norm(B, 2)  # [[I, B], [B^T, I]] is SPD, Jacobi radius 0.95
+    Z = np.zeros((n, n))
+    Dd = np.eye(2 * n)
+    Lb = np.block([[Z, Z], [-B.T, Z]])
+    Ub = np.block([[Z, -B], [Z, Z]])
+
+    def rho(w):
+        M = np.linalg.solve(Dd - w * Lb, w * Ub + (1 - w) * Dd)
+        return float(np.abs(np.linalg.eigvals(M)).max())
+
+    w_rule = am.omega_update(rho(1.0), 1.0, 1.99)
+    ws = np.linspace(1.0, 1.99, 2000)
+    w_best = ws[int(np.argmin([rho(w) for w in ws]))]
+    assert abs(w_rule - w_best) < 2e-3
+    assert rho(w_rule) < rho(1.0)

@@ -286,3 +286,43 @@ def test_thermal_temperature_at_centroids_against_hand_values():
         np.testing.assert_array_equal(e0[:, 0], T)
         np.testing.assert_array_equal(e0[:, 1], T)
         assert not np.any(e0[:, 2])
+
+
+def test_mode_I_field_closed_forms_on_special_rays():
+    """eq. (surfingloading): ahead of the tip (theta = 0) the opening component vanishes and
+    u_x = K/(2 mu) sqrt(r/(2 pi)) (kappa - 1); on the crack faces (theta = pi) u_x = 0 and
+    u_y = K/(2 mu) sqrt(r/(2 pi)) (kappa + 1); kappa = (3 - nu)/(1 + nu) in plane stress."""
+    mat = fe.Material(nu=0.3, plane="stress")
+    K, r = 1.7, 0.09
+    kappa = (3 - 0.3) / 1.3
+    a = K / (2 * mat.mu) * np.sqrt(r / (2 * np.pi))
+    ux, uy = fe.mode_I_displacement(mat, K, r, 0.0)
+    assert abs(uy) < 1e-15 and abs(ux - a * (kappa - 1)) < 1e-14
+    ux, uy = fe.mode_I_displacement(mat, K, -r, 0.0)
+    assert abs(ux) < 1e-15 and abs(uy - a * (kappa + 1)) < 1e-14
+    ux, uy = fe.mode_I_displacement(mat, K, 0.0, r)  # theta = pi/2
+    assert abs(ux - a * kappa / np.sqrt(2)) < 1e-14 and abs(uy - a * kappa / np.sqrt(2)) < 1e-14
+    ux2, uy2 = fe.mode_I_displacement(mat, K, 0.0, -r)  # mirror: u_x even, u_y odd in y
+    assert abs(ux2 - ux) < 1e-15 and abs(uy2 + uy) < 1e-15
+
+
+@pytest.mark.parametrize("kind", ["right", "crossed"])
+def test_mode_I_field_is_in_equilibrium(kind):
+    """Away from the tip the Mode-I field solves the homogeneous Lame equations: the FE solution
+    with that field as Dirichlet data on a square beside the tip converges to it at O(h^2)
+    (a wrong kappa, sign or angle convention leaves an O(1) error)."""
+    from oracle import am
+
+    errs = []
+    for n in (8, 16, 32):
+        w = W.Workload(name="eq", kind=kind, nx=n, ny=n, x0=0.5, y0=-0.5, lx=1.0, ly=1.0,
+                       plane="stress", fixed={e: {"ux": 1.0, "uy": 1.0} for e in W.EDGES},
+                       mode_I=dict(KI=1.0, x_tip0=0.0, v=0.0, y_line=0.0))
+        p = Problem(w)
+        p.lift(0.0)
+        u = am.solve_u(p, p.alpha, 0.0)
+        ux, uy = fe.mode_I_displacement(p.mat, 1.0, p.mesh.xy[:, 0], p.mesh.xy[:, 1])
+        ex = np.stack([ux, uy], axis=1)
+        errs.append(np.abs(u - ex).max() / np.abs(ex).max())
+    assert errs[-1] < 1e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0
