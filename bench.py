@@ -86,6 +86,9 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=256,
                     help="instances in the batch leg (0: no batch leg)")
     ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--configs", action="store_true",
+                    help="whole schedules of the bar 128x16, the notched square 512^2 and the "
+                         "thermal slab 1024x256, FP64 and mixed, then exit")
     ap.add_argument("--omega-sweep", action="store_true",
                     help="alternate-minimization iterations versus omega (Tables 1-3) on the "
                          "surfing, bar and thermal workloads, then exit")
@@ -394,6 +397,49 @@ def serve_record(args, ctx):
     }
 
 
+def configs_record(ctx):
+    """Whole load schedules of the other configurations in mixed precision, and their steps before
+    damage growth in plain FP64: load steps/s, AM iterations, steps not converged, the FP64/mixed
+    time ratio over the same steps and the largest relative energy difference of mixed against
+    FP64 over those steps."""
+    import workloads as W
+    from paper_1511_08463_gb300 import sim as S
+
+    cases = {"bar_128x16_AT1_AM": W.bar(),
+             "notched_512_crossed_AT1_ORAM_omega1.5": W.notched_square(n=512),
+             "thermal_1024x256_AT1_ORAM_omega1.6": W.thermal_shock()}
+    FP64_CONFIG_STEPS = {"bar_128x16_AT1_AM": 20, "notched_512_crossed_AT1_ORAM_omega1.5": 30,
+                         "thermal_1024x256_AT1_ORAM_omega1.6": 9}
+    out = {}
+    for name, w in cases.items():
+        rec = {}
+        energies = {}
+        for prec in ("fp64", "mixed"):
+            g = S.Sim(w, ctx)
+            o = S.make_opts(omega=w.omega, precision=prec, am_maxit=AM_MAXIT)
+            # plain FP64 runs the steps before damage growth only (the growth steps take
+            # minutes in FP64 at these sizes); mixed runs the whole schedule
+            loads = w.loads if prec == "mixed" else w.loads[:FP64_CONFIG_STEPS[name]]
+            t0 = time.perf_counter()
+            reps = [g.load_step(*ld, o, allow_notconv=True) for ld in loads]
+            dt = time.perf_counter() - t0
+            g.close()
+            energies[prec] = [r["energy"][2] for r in reps]
+            if prec == "mixed":
+                mixed_secs = [r["seconds"] for r in reps]
+            rec[prec] = {"load_steps": len(reps), "seconds": dt, "load_steps_per_s": len(reps) / dt,
+                         "am_iters": sum(r["am_iters"] for r in reps),
+                         "max_am_iters_per_step": max(r["am_iters"] for r in reps),
+                         "not_ok": sum(1 for r in reps if r["status"] != 0)}
+        nf = len(energies["fp64"])
+        rec["mixed_speedup_same_steps"] = (rec["fp64"]["seconds"] /
+                                           sum(mixed_secs[:nf]))
+        rec["max_rel_energy_diff_mixed_vs_fp64"] = max(
+            abs(a - b) / max(abs(b), 1e-300) for a, b in zip(energies["mixed"], energies["fp64"]))
+        out[name] = rec
+    return out
+
+
 def omega_sweep_record(ctx):
     """AM iterations and time of whole schedules for fixed omega in 1.0 .. 1.8 and the automated
     omega, on the three workloads of the paper's over-relaxation tables: surfing (Table 1), the
@@ -481,6 +527,11 @@ def run_ours(args):
     from paper_1511_08463_gb300 import sim as S
 
     lib = B.load()
+    if args.configs:
+        rec = configs_record(S.Context(local))
+        if rank == 0:
+            print(json.dumps({"configs": rec}), flush=True)
+        return 0
     if args.omega_sweep:
         rec = omega_sweep_record(S.Context(local))
         if rank == 0:

@@ -348,16 +348,19 @@ pf_status pf_op_elastic_apply(pf_sim* sim, int precision, int masked, const void
 
 /* r = -(E_u) = f - K(alpha) u on free dofs, 0 on prescribed dofs, for the resident u, alpha and
  * the current load (thermal load vector included).  r: device, 2*n_nodes doubles, 16-byte
- * aligned (PF_EINVAL otherwise).
- * *norm2 (host) receives ||r||^2. */
-pf_status pf_op_elastic_residual(pf_sim* sim, double* r, double* norm2, void* stream);
+ * aligned (PF_EINVAL otherwise).  *norm2 (host) receives ||r||^2.  precision PF_FP64: FP64
+ * arithmetic (the plain FP64 path); PF_MIXED: the arithmetic the mixed path uses for its FP64
+ * residuals, double-float (pairs of FP32 numbers, ~48 significand bits) on the same FP64 data. */
+pf_status pf_op_elastic_residual(pf_sim* sim, int precision, double* r, double* norm2,
+                                 void* stream);
 
 /* Damage gradient E_alpha = H alpha + g0 at the resident u, alpha (Section 1.2 and eq.
  * helmholtz), its MCP Fischer-Burmeister residual Phi on the box [lower, upper] (Section 2.4)
  * and the active-set flags (eq. reducedis; 1 = active).  F, Phi: device, n_nodes doubles;
- * active: device, n_nodes bytes (may be NULL).  *phi_norm2 (host) receives ||Phi||^2. */
-pf_status pf_op_damage_gradient(pf_sim* sim, double* F, double* Phi, uint8_t* active,
-                                double* phi_norm2, void* stream);
+ * active: device, n_nodes bytes (may be NULL).  *phi_norm2 (host) receives ||Phi||^2.
+ * precision: as for pf_op_elastic_residual (PF_MIXED: H alpha + g0 in double-float). */
+pf_status pf_op_damage_gradient(pf_sim* sim, int precision, double* F, double* Phi,
+                                uint8_t* active, double* phi_norm2, void* stream);
 
 /* y = H(q(u)) x, the damage Hessian E_aa at the resident u (precision as above; n_nodes
  * values). */

@@ -126,8 +126,8 @@ _SIGS = {
     "pf_destroy": (None, [_VP]),
     "pf_set_load": (C.c_int, [_VP, C.POINTER(pf_load)]),
     "pf_op_elastic_apply": (C.c_int, [_VP, C.c_int, C.c_int, _VP, _VP, _VP]),
-    "pf_op_elastic_residual": (C.c_int, [_VP, _VP, C.POINTER(C.c_double), _VP]),
-    "pf_op_damage_gradient": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(C.c_double), _VP]),
+    "pf_op_elastic_residual": (C.c_int, [_VP, C.c_int, _VP, C.POINTER(C.c_double), _VP]),
+    "pf_op_damage_gradient": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.POINTER(C.c_double), _VP]),
     "pf_op_damage_apply": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP]),
     "pf_op_coupling_apply": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP]),
     "pf_op_u_solve": (C.c_int, [_VP, C.POINTER(pf_solver_opts), _VP, C.POINTER(pf_step_report)]),

@@ -40,6 +40,18 @@ static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
 
 template <class T, int K, int M, bool D>
 static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>& a) {
+  if constexpr (std::is_same<T, double>::value && (M == M_GRAD || M == M_TRIAL)) {
+    if (a.df) {  // the mixed path's gradient / trial point: FP64 data, double-float arithmetic
+      DamageOp<T, K, M, D, dfloat> op;
+      op.g = g;
+      op.m = m;
+      op.cs = make_consts<dfloat>(g, m);
+      op.args = a;
+      launch_op(s, op, kclass(M == M_GRAD ? KC_DM_GRAD_DF : KC_DM_TRIAL_DF, true, a.coarse),
+                damage_bytes<T>(g, M, a));
+      return;
+    }
+  }
   DamageOp<T, K, M, D> op;
   op.g = g;
   op.m = m;

@@ -39,6 +39,17 @@ static void launch_op(cudaStream_t s, const Op& op, int id, double bytes) {
 
 template <class T, int K, int C, int M, bool E, bool D>
 static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>& a) {
+  if constexpr (std::is_same<T, double>::value && M == M_RESID) {
+    if (a.df) {  // the mixed path's physical residual: FP64 data, double-float arithmetic
+      ElasticOp<T, K, C, M, E, D, dfloat> op;
+      op.g = g;
+      op.m = m;
+      op.cs = make_consts<dfloat>(g, m);
+      op.args = a;
+      launch_op(s, op, kclass(KC_EL_RESID_DF, true, a.coarse), elastic_bytes<T>(g, C, M, a));
+      return;
+    }
+  }
   ElasticOp<T, K, C, M, E, D> op;
   op.g = g;
   op.m = m;

@@ -67,7 +67,8 @@ void harvest() {
 const char* BASE_NAMES[KC_BASE_COUNT] = {
     "elastic_apply", "elastic_masked", "elastic_resb", "elastic_resid", "elastic_cheb",
     "damage_apply", "damage_masked", "damage_resb", "damage_cheb", "damage_grad", "damage_trial",
-    "vector", "reduce", "transfer", "setup", "coarse_solve", "tail_vcycle"};
+    "vector", "reduce", "transfer", "setup", "coarse_solve", "tail_vcycle",
+    "elastic_resid_df", "damage_grad_df", "damage_trial_df"};
 
 }  // namespace
 

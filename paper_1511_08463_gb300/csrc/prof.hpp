@@ -16,7 +16,9 @@ namespace pf {
 enum KernelClass : int {
   KC_EL_APPLY = 0, KC_EL_MASKED, KC_EL_RESB, KC_EL_RESID, KC_EL_CHEB,
   KC_DM_APPLY, KC_DM_MASKED, KC_DM_RESB, KC_DM_CHEB, KC_DM_GRAD, KC_DM_TRIAL,
-  KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_TAIL, KC_BASE_COUNT
+  KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_TAIL,
+  KC_EL_RESID_DF, KC_DM_GRAD_DF, KC_DM_TRIAL_DF,  // FP64 in/out, double-float arithmetic
+  KC_BASE_COUNT
 };
 // class id = base + KC_BASE_COUNT * (precision * KC_LEVELS + multigrid level), so that one class
 // is one kernel at one problem size (deeper levels than KC_LEVELS - 1 share the last class)

@@ -842,6 +842,7 @@ pf_status physical_residual(pf_sim& s, cudaStream_t st, const double* u, double*
   a.eig = s.eig;
   a.y = r;
   a.slot = slot(s, S_RES);
+  a.df = s.df;
   launch_elastic<double>(st, s.lv[0].g, s.m, COEF_ALPHA, M_RESID, s.thermal, false, a);
   double v;
   TRY(read_scalars(s, st, S_RES, 1, &v));
@@ -906,6 +907,7 @@ pf_status grad_at(pf_sim& s, cudaStream_t st, const double* x, double zeta, doub
   a.rhs = rhs;
   a.act = act;
   a.slot = slot(s, S_PHI);
+  a.df = s.df;
   launch_damage<double>(st, s.lv[0].g, s.m, M_GRAD, false, a);
   return read_scalars(s, st, S_PHI, 2, out);
 }
@@ -925,6 +927,7 @@ pf_status trial_at(pf_sim& s, cudaStream_t st, const double* x, const double* d,
   a.act = s.acttr;
   a.xt = s.xtr;
   a.slot = slot(s, S_PHI);
+  a.df = s.df;
   launch_damage<double>(st, s.lv[0].g, s.m, M_TRIAL, false, a);
   return read_scalars(s, st, S_PHI, 2, out);
 }
@@ -1488,6 +1491,7 @@ void apply_tiles(pf_sim& s) {
 
 // the per-call solver settings that pf_load_step derives from the options
 void apply_opts(pf_sim& s, const pf_solver_opts& o) {
+  s.df = o.precision == PF_MIXED;
   s.use_graphs = o.use_graphs != 0;
   s.nl_active = o.mg_levels_max > 0 ? std::min<int>(o.mg_levels_max, (int)s.lv.size())
                                     : (int)s.lv.size();
@@ -2070,27 +2074,32 @@ pf_status pf_op_elastic_apply(pf_sim* s, int precision, int masked, const void* 
   return PF_OK;
 }
 
-pf_status pf_op_elastic_residual(pf_sim* s, double* r, double* norm2, void* stream) {
+pf_status pf_op_elastic_residual(pf_sim* s, int precision, double* r, double* norm2,
+                                 void* stream) {
   if (!s || !r) return fail(PF_EINVAL, "null argument");
+  if (precision != PF_FP64 && precision != PF_MIXED) return fail(PF_EINVAL, "unknown precision");
   if (reinterpret_cast<uintptr_t>(r) % 16) return fail(PF_EINVAL, "r must be 16-byte aligned");
   CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   CU(cudaSetDevice(s->ctx->device));
   double nrm;
+  s->df = precision == PF_MIXED;
   TRY(physical_residual(*s, static_cast<cudaStream_t>(stream), s->u, r, &nrm));
   if (norm2) *norm2 = nrm * nrm;
   return PF_OK;
 }
 
-pf_status pf_op_damage_gradient(pf_sim* s, double* F, double* Phi, uint8_t* active,
-                                double* phi_norm2, void* stream) {
+pf_status pf_op_damage_gradient(pf_sim* s, int precision, double* F, double* Phi,
+                                uint8_t* active, double* phi_norm2, void* stream) {
   if (!s || !F || !Phi) return fail(PF_EINVAL, "null argument");
+  if (precision != PF_FP64 && precision != PF_MIXED) return fail(PF_EINVAL, "unknown precision");
   CLAIM(s);
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   damage_q(st, s->lv[0].g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, nullptr, nullptr);
   double v[2];
+  s->df = precision == PF_MIXED;
   TRY(grad_at(*s, st, s->alpha, 1e-10, F, Phi, s->rhstr, active ? active : s->acttr, v));
   if (phi_norm2) *phi_norm2 = v[0];
   return PF_OK;
@@ -2152,6 +2161,7 @@ pf_status pf_op_u_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf_ste
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   s->r_scale = 0.0;
+  s->df = o->precision == PF_MIXED;
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();
@@ -2176,6 +2186,7 @@ pf_status pf_op_alpha_solve(pf_sim* s, const pf_solver_opts* o, void* stream, pf
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   s->phi_scale = 0.0;
+  s->df = o->precision == PF_MIXED;
   s->use_graphs = o->use_graphs != 0;
   s->nl_active = o->mg_levels_max > 0 ? std::min<int>(o->mg_levels_max, (int)s->lv.size())
                                       : (int)s->lv.size();

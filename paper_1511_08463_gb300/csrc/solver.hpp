@@ -138,6 +138,9 @@ struct pf_sim {
   int cg_tail[2][2] = {};
   int cg_tiles[2][2] = {};  // tile configuration the graph was captured with
   int tile_fine = 0, tile_coarse = 0;  // FP32 stencil tile heights (0: default)
+  // the FP64-data kernels (physical residual, damage gradient and trial point) compute in
+  // double-float: set for PF_MIXED solves, whose refinement only needs ~14 digits
+  bool df = false;
   double* host = nullptr;  // pinned read-back slot from the context's pool
   ~pf_sim() {
     if (host && ctx) ctx->give_slot(host);

@@ -14,6 +14,9 @@
 //   DamageOp:  H p = sum_T (w_T M_T + c1 L_T) p_T with w_T = q_T + c2 (eq. helmholtz), and for
 //              the gradient E_alpha = H alpha + g0, g0_T = (c3 - q_T) |T| / 3 per node.
 #pragma once
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "mg_core.cuh"
 
 namespace pf {
@@ -196,75 +199,129 @@ struct ElasticArgs {
   T* dout;            // M_CHEB: new d
   RedSlot slot;
   int coarse;         // launch accounting: multigrid level (0 = finest)
+  int df;             // M_RESID with T = double: 1 computes in double-float (the mixed path)
 };
 
-template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT>
+// Arithmetic helpers shared by the operators.  For float and double they are the plain
+// expressions; for double-float they leave out zero terms and use exact additions for the
+// integer weights +-1, +-2 of the gradient tables instead of general products.
+template <class C>
+__device__ __forceinline__ C to_c(double v) { return C(v); }
+template <class C>
+__device__ __forceinline__ C to_c(float v) { return C(v); }
+template <int c, class C>
+__device__ __forceinline__ C imul(C v) {
+  if constexpr (std::is_same<C, dfloat>::value) {
+    static_assert(c >= -2 && c <= 2, "gradient weights are small integers");
+    if constexpr (c == 0) return C(0);
+    else if constexpr (c == 1) return v;
+    else if constexpr (c == -1) return -v;
+    else if constexpr (c == 2) return v + v;
+    else return -(v + v);
+  } else {
+    return C(c) * v;
+  }
+}
+template <int a, int b, int c, class C>
+__device__ __forceinline__ C gsum(C x, C y, C z) {
+  if constexpr (std::is_same<C, dfloat>::value) {
+    C s = C(0);
+    bool h = false;
+    if constexpr (a != 0) {
+      s = imul<a>(x);
+      h = true;
+    }
+    if constexpr (b != 0) {
+      s = h ? s + imul<b>(y) : imul<b>(y);
+      h = true;
+    }
+    if constexpr (c != 0) s = h ? s + imul<c>(z) : imul<c>(z);
+    return s;
+  } else {
+    return C(a) * x + C(b) * y + C(c) * z;
+  }
+}
+// storage value of a computed one
+template <class T, class C>
+__device__ __forceinline__ T to_t(C v) {
+  if constexpr (std::is_same<C, dfloat>::value) return T(double(v));
+  else return T(v);
+}
+
+// C: the arithmetic type; dfloat for the FP64 physical residual of the mixed path (inputs and
+// outputs stay FP64, T = double)
+template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT, class C = T>
 struct ElasticOp {
   using Scalar = T;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
   static constexpr bool RED_MAX = false;
-  using RT = T;  // per-thread partial sums in the operator's precision
+  // per-thread partial sums in the operator's precision (FP64 for double-float)
+  using RT = typename std::conditional<std::is_same<C, dfloat>::value, double, C>::type;
   struct V {
-    T ux, uy, a;
+    C ux, uy, a;
   };
-  using ET = T;
+  using ET = C;
   static constexpr int NRC = 3;
   struct R {
-    T c[3];  // w A0 eps: sxx, syy, sxy
+    C c[3];  // w A0 eps: sxx, syy, sxy
   };
   struct Acc {
-    T ax, bx, ay, by;
+    C ax, bx, ay, by;
   };
   Grid g;
   Mat m;
-  Consts<T> cs;
+  Consts<C> cs;
   ElasticArgs<T> args;
 
-  __device__ static V zero() { return V{T(0), T(0), T(0)}; }
-  __device__ static Acc acc0() { return Acc{T(0), T(0), T(0), T(0)}; }
+  __device__ static V zero() { return V{C(0), C(0), C(0)}; }
+  __device__ static Acc acc0() { return Acc{C(0), C(0), C(0), C(0)}; }
 
   __device__ V load(int node, int X2, int Y2) const {
     V v;
-    v.ux = v.uy = T(0);  // M_CHEB without x: smoothing from zero
+    v.ux = v.uy = C(0);  // M_CHEB without x: smoothing from zero
     if (args.x) {
       const Pair<T> u = ld_pair(args.x, node);
-      v.ux = u.x;
-      v.uy = u.y;
+      v.ux = to_c<C>(u.x);
+      v.uy = to_c<C>(u.y);
     }
-    if (MODE == M_CHEB && args.xc) {
-      v.ux += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0);
-      v.uy += prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 1);
+    if constexpr (MODE == M_CHEB) {
+      if (args.xc) {
+        v.ux += to_c<C>(prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0));
+        v.uy += to_c<C>(prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 1));
+      }
     }
     if (MODE != M_APPLY && MODE != M_RESID) {
-      if (is_fixed(g, X2, Y2, 0)) v.ux = T(0);
-      if (is_fixed(g, X2, Y2, 1)) v.uy = T(0);
+      if (is_fixed(g, X2, Y2, 0)) v.ux = C(0);
+      if (is_fixed(g, X2, Y2, 1)) v.uy = C(0);
     }
-    v.a = COEF == COEF_ALPHA ? args.alpha[node] : T(0);
+    v.a = COEF == COEF_ALPHA ? to_c<C>(args.alpha[node]) : C(0);
     return v;
   }
 
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
-    if (!valid) return R{{T(0), T(0), T(0)}};
+    if (!valid) return R{{C(0), C(0), C(0)}};
     constexpr int NE = elems_per_cell(KIND);
-    T w;
+    constexpr int a0 = gx(KIND, t, 0), a1 = gx(KIND, t, 1), a2 = gx(KIND, t, 2);
+    constexpr int b0 = gy(KIND, t, 0), b1 = gy(KIND, t, 1), b2 = gy(KIND, t, 2);
+    C w;
     if (COEF == COEF_ALPHA)
-      w = abar3<T>(n0.a, n1.a, n2.a, cs.k_ell) * cs.area;
+      w = abar3<C>(n0.a, n1.a, n2.a, cs.k_ell) * cs.area;
     else
-      w = args.coef[cell * NE + t] * cs.area;
-    const T ihx = cs.ihx, ihy = cs.ihy;
-    T sx = T(gx(KIND, t, 0)) * n0.ux + T(gx(KIND, t, 1)) * n1.ux + T(gx(KIND, t, 2)) * n2.ux;
-    T sy = T(gy(KIND, t, 0)) * n0.uy + T(gy(KIND, t, 1)) * n1.uy + T(gy(KIND, t, 2)) * n2.uy;
-    T s1 = T(gy(KIND, t, 0)) * n0.ux + T(gy(KIND, t, 1)) * n1.ux + T(gy(KIND, t, 2)) * n2.ux;
-    T s2 = T(gx(KIND, t, 0)) * n0.uy + T(gx(KIND, t, 1)) * n1.uy + T(gx(KIND, t, 2)) * n2.uy;
-    T exx = ihx * sx, eyy = ihy * sy, gxy = ihy * s1 + ihx * s2;
+      w = to_c<C>(args.coef[cell * NE + t]) * cs.area;
+    const C ihx = cs.ihx, ihy = cs.ihy;
+    C sx = gsum<a0, a1, a2>(n0.ux, n1.ux, n2.ux);
+    C sy = gsum<b0, b1, b2>(n0.uy, n1.uy, n2.uy);
+    C s1 = gsum<b0, b1, b2>(n0.ux, n1.ux, n2.ux);
+    C s2 = gsum<a0, a1, a2>(n0.uy, n1.uy, n2.uy);
+    C exx = ihx * sx, eyy = ihy * sy, gxy = ihy * s1 + ihx * s2;
     if (EIGEN) {
-      T e0 = T(args.eig[cj * NE + t]);
+      C e0 = to_c<C>(args.eig[cj * NE + t]);
       exx -= e0;
       eyy -= e0;
     }
-    const T lam = cs.lam, l2m = cs.lam2mu, mu = cs.mu;
+    const C lam = cs.lam, l2m = cs.lam2mu, mu = cs.mu;
     return R{{w * (l2m * exx + lam * eyy), w * (lam * exx + l2m * eyy), w * mu * gxy}};
   }
 
@@ -272,45 +329,48 @@ struct ElasticOp {
   __device__ void add(Acc& a, const R& r) const {
     constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
     if (cx != 0) {
-      a.ax += T(cx) * r.c[0];
-      a.ay += T(cx) * r.c[2];
+      a.ax += imul<cx>(r.c[0]);
+      a.ay += imul<cx>(r.c[2]);
     }
     if (cy != 0) {
-      a.bx += T(cy) * r.c[2];
-      a.by += T(cy) * r.c[1];
+      a.bx += imul<cy>(r.c[2]);
+      a.by += imul<cy>(r.c[1]);
     }
   }
 
   __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
                         RT (&red)[NR > 0 ? NR : 1]) const {
-    T fx = cs.ihx * a.ax + cs.ihy * a.bx;
-    T fy = cs.ihx * a.ay + cs.ihy * a.by;
+    C fx = cs.ihx * a.ax + cs.ihy * a.bx;
+    C fy = cs.ihx * a.ay + cs.ihy * a.by;
     bool f0 = false, f1 = false;
     if (MODE != M_APPLY) {
       f0 = is_fixed(g, X2, Y2, 0);
       f1 = is_fixed(g, X2, Y2, 1);
     }
-    if (MODE == M_APPLY || MODE == M_MASKED) {
-      T yx = f0 ? T(0) : fx, yy = f1 ? T(0) : fy;
-      st_pair(args.y, node, yx, yy);
-      if (DOT) red[0] += own.ux * yx + own.uy * yy;
-    } else if (MODE == M_RESB) {
-      const Pair<T> b = ld_pair(args.b, node);
-      T rx = f0 ? T(0) : b.x - fx, ry = f1 ? T(0) : b.y - fy;
+    if constexpr (MODE == M_RESID) {
+      const T rx = f0 ? T(0) : to_t<T>(-fx), ry = f1 ? T(0) : to_t<T>(-fy);
       st_pair(args.y, node, rx, ry);
-      if (DOT) red[0] += rx * rx + ry * ry;
-    } else if (MODE == M_RESID) {
-      T rx = f0 ? T(0) : -fx, ry = f1 ? T(0) : -fy;
-      st_pair(args.y, node, rx, ry);
-      red[0] += rx * rx + ry * ry;
-    } else if (MODE == M_CHEB) {
-      const Pair<T> b = ld_pair(args.b, node), di = ld_pair(args.dinv, node);
-      const Pair<T> p = args.d ? ld_pair(args.d, node) : Pair<T>{T(0), T(0)};
-      T rx = b.x - fx, ry = b.y - fy;
-      T dx = f0 ? T(0) : args.cd * p.x + args.cr * di.x * rx;
-      T dy = f1 ? T(0) : args.cd * p.y + args.cr * di.y * ry;
-      st_pair(args.dout, node, dx, dy);
-      st_pair(args.y, node, own.ux + dx, own.uy + dy);
+      red[0] += RT(rx) * RT(rx) + RT(ry) * RT(ry);
+    } else {
+      static_assert(std::is_same<C, T>::value, "only the physical residual runs in double-float");
+      if (MODE == M_APPLY || MODE == M_MASKED) {
+        T yx = f0 ? T(0) : fx, yy = f1 ? T(0) : fy;
+        st_pair(args.y, node, yx, yy);
+        if (DOT) red[0] += own.ux * yx + own.uy * yy;
+      } else if (MODE == M_RESB) {
+        const Pair<T> b = ld_pair(args.b, node);
+        T rx = f0 ? T(0) : b.x - fx, ry = f1 ? T(0) : b.y - fy;
+        st_pair(args.y, node, rx, ry);
+        if (DOT) red[0] += rx * rx + ry * ry;
+      } else if (MODE == M_CHEB) {
+        const Pair<T> b = ld_pair(args.b, node), di = ld_pair(args.dinv, node);
+        const Pair<T> p = args.d ? ld_pair(args.d, node) : Pair<T>{T(0), T(0)};
+        T rx = b.x - fx, ry = b.y - fy;
+        T dx = f0 ? T(0) : args.cd * p.x + args.cr * di.x * rx;
+        T dy = f1 ? T(0) : args.cd * p.y + args.cr * di.y * ry;
+        st_pair(args.dout, node, dx, dy);
+        st_pair(args.y, node, own.ux + dx, own.uy + dy);
+      }
     }
   }
 };
@@ -338,67 +398,79 @@ struct DamageArgs {
   uint8_t* act;         // M_GRAD/M_TRIAL: active flags written
   RedSlot slot;
   int coarse;           // launch accounting: multigrid level (0 = finest)
+  int df;               // M_GRAD/M_TRIAL: 1 computes H x + g0 in double-float (the mixed path)
 };
 
-template <class T, int KIND_, int MODE, bool DOT>
+// C: the arithmetic type; dfloat for the FP64 damage gradient / trial point of the mixed path
+// (inputs and outputs stay FP64, T = double)
+template <class T, int KIND_, int MODE, bool DOT, class C = T>
 struct DamageOp {
   using Scalar = T;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
   static constexpr bool RED_MAX = false;
-  using RT = T;
+  static constexpr bool DF = std::is_same<C, dfloat>::value;
+  using RT = typename std::conditional<DF, double, C>::type;
   struct V {
-    T p;
+    C p;
   };
-  using ET = T;
+  using ET = C;
   static constexpr int NRC = 4;
   struct R {
-    T c[4];  // P, M, X, Y
+    C c[4];  // P, M, X, Y
   };
   struct Acc {
-    T P, M, X, Y;
+    C P, M, X, Y;
   };
   Grid g;
   Mat m;
-  Consts<T> cs;
+  Consts<C> cs;
   DamageArgs<T> args;
 
-  __device__ static V zero() { return V{T(0)}; }
-  __device__ static Acc acc0() { return Acc{T(0), T(0), T(0), T(0)}; }
+  __device__ static V zero() { return V{C(0)}; }
+  __device__ static Acc acc0() { return Acc{C(0), C(0), C(0), C(0)}; }
 
   __device__ double upper(int X2, int Y2, double l) const {
     return is_fixed(g, X2, Y2, 2) ? l : 1.0;
+  }
+  // the line-search point of M_TRIAL in FP64: clip(x + mu d) to the node's box
+  __device__ double trial_value(int node, int X2, int Y2) const {
+    double l = args.lo[node], h = upper(X2, Y2, l);
+    double z = double(args.x[node]) + double(args.cd) * double(args.d[node]);
+    return fmin(fmax(z, l), h);
   }
 
   __device__ V load(int node, int X2, int Y2) const {
     V v;
     if (MODE == M_TRIAL) {
-      double l = args.lo[node], h = upper(X2, Y2, l);
-      double z = double(args.x[node]) + double(args.cd) * double(args.d[node]);
-      v.p = T(fmin(fmax(z, l), h));
+      v.p = to_c<C>(T(trial_value(node, X2, Y2)));
     } else {
-      v.p = args.x ? args.x[node] : T(0);  // M_CHEB without x: smoothing from zero
-      if (MODE == M_CHEB && args.xc) v.p += prolong_value(g, args.gc, 1, args.xc, node, X2, Y2, 0);
-      if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = T(0);
+      v.p = args.x ? to_c<C>(args.x[node]) : C(0);  // M_CHEB without x: smoothing from zero
+      if constexpr (MODE == M_CHEB) {
+        if (args.xc) v.p += to_c<C>(prolong_value(g, args.gc, 1, args.xc, node, X2, Y2, 0));
+      }
+      if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = C(0);
     }
     return v;
   }
 
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
-    if (!valid) return R{{T(0), T(0), T(0), T(0)}};
+    if (!valid) return R{{C(0), C(0), C(0), C(0)}};
     constexpr int NE = elems_per_cell(KIND);
-    const T area = cs.area;
-    T wt = args.w[cell * NE + t];
-    T qT = wt;
+    constexpr int a0 = gx(KIND, t, 0), a1 = gx(KIND, t, 1), a2 = gx(KIND, t, 2);
+    constexpr int b0 = gy(KIND, t, 0), b1 = gy(KIND, t, 1), b2 = gy(KIND, t, 2);
+    const C area = cs.area;
+    C wt = to_c<C>(args.w[cell * NE + t]);
+    C qT = wt;
     if (MODE == M_GRAD || MODE == M_TRIAL) wt = wt + cs.c2;
-    T me = wt * area * T(1.0 / 12.0);
-    T S = n0.p + n1.p + n2.p;
-    T gpx = cs.ihx * (T(gx(KIND, t, 0)) * n0.p + T(gx(KIND, t, 1)) * n1.p + T(gx(KIND, t, 2)) * n2.p);
-    T gpy = cs.ihy * (T(gy(KIND, t, 0)) * n0.p + T(gy(KIND, t, 1)) * n1.p + T(gy(KIND, t, 2)) * n2.p);
-    T c1a = cs.c1 * area;
-    T P = me * S;
-    if (MODE == M_GRAD || MODE == M_TRIAL) P += (cs.c3 - qT) * area * T(1.0 / 3.0);
+    C me = wt * area * C(1.0 / 12.0);
+    C S = n0.p + n1.p + n2.p;
+    C gpx = cs.ihx * gsum<a0, a1, a2>(n0.p, n1.p, n2.p);
+    C gpy = cs.ihy * gsum<b0, b1, b2>(n0.p, n1.p, n2.p);
+    C c1a = cs.c1 * area;
+    C P = me * S;
+    if (MODE == M_GRAD || MODE == M_TRIAL) P += (cs.c3 - qT) * area * C(1.0 / 3.0);
     return R{{P, me, c1a * cs.ihx * gpx, c1a * cs.ihy * gpy}};
   }
 
@@ -407,31 +479,19 @@ struct DamageOp {
     constexpr int cx = gx(KIND, t, k), cy = gy(KIND, t, k);
     a.P += r.c[0];
     a.M += r.c[1];
-    if (cx != 0) a.X += T(cx) * r.c[2];
-    if (cy != 0) a.Y += T(cy) * r.c[3];
+    if (cx != 0) a.X += imul<cx>(r.c[2]);
+    if (cy != 0) a.Y += imul<cy>(r.c[3]);
   }
 
   __device__ void store(int node, int X2, int Y2, const V& own, const Acc& a,
                         RT (&red)[NR > 0 ? NR : 1]) const {
-    T f = a.P + a.M * own.p + a.X + a.Y;
-    if (MODE == M_APPLY) {
-      args.y[node] = f;
-      if (DOT) red[0] += own.p * f;
-    } else if (MODE == M_MASKED) {
-      T v = (args.excl && args.excl[node]) ? T(0) : f;
-      args.y[node] = v;
-      if (DOT) red[0] += own.p * v;
-    } else if (MODE == M_RESB) {
-      T r = (args.excl && args.excl[node]) ? T(0) : args.b[node] - f;
-      args.y[node] = r;
-      if (DOT) red[0] += r * r;
-    } else if (MODE == M_CHEB) {
-      T dp = args.d ? args.d[node] : T(0);
-      T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
-      args.dout[node] = dn;
-      args.y[node] = own.p + dn;
-    } else {  // M_GRAD / M_TRIAL (T = double)
-      double xv = double(own.p), F = double(f);
+    C f = a.P + a.M * own.p + a.X + a.Y;
+    if constexpr (MODE == M_GRAD || MODE == M_TRIAL) {  // T = double
+      // the node's own value exactly as FP64 (a double-float copy keeps 48 bits)
+      double xv;
+      if constexpr (DF) xv = MODE == M_TRIAL ? trial_value(node, X2, Y2) : double(args.x[node]);
+      else xv = double(own.p);
+      const double F = to_t<double>(f);
       double l = args.lo[node], h = upper(X2, Y2, l);
       double ph = mcp_phi(xv, F, l, h);
       // eq. reducedis with both bounds; a single-point box counts as lower-active
@@ -442,9 +502,28 @@ struct DamageOp {
       args.dout[node] = T(ph);
       args.rhs[node] = active ? T(0) : T(-F);
       args.act[node] = lower ? 1 : (upper ? 2 : 0);
-      if (MODE == M_TRIAL) args.xt[node] = own.p;
-      red[0] += T(ph * ph);
-      red[1] += active ? T(0) : T(F * F);
+      if (MODE == M_TRIAL) args.xt[node] = T(xv);
+      red[0] += RT(ph * ph);
+      red[1] += active ? RT(0) : RT(F * F);
+    } else {
+      static_assert(!DF, "only the gradient and the trial point run in double-float");
+      if (MODE == M_APPLY) {
+        args.y[node] = f;
+        if (DOT) red[0] += own.p * f;
+      } else if (MODE == M_MASKED) {
+        T v = (args.excl && args.excl[node]) ? T(0) : f;
+        args.y[node] = v;
+        if (DOT) red[0] += own.p * v;
+      } else if (MODE == M_RESB) {
+        T r = (args.excl && args.excl[node]) ? T(0) : args.b[node] - f;
+        args.y[node] = r;
+        if (DOT) red[0] += r * r;
+      } else if (MODE == M_CHEB) {
+        T dp = args.d ? args.d[node] : T(0);
+        T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
+        args.dout[node] = dn;
+        args.y[node] = own.p + dn;
+      }
     }
   }
 };

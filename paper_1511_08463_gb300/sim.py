@@ -181,21 +181,23 @@ class Sim:
                                              C.c_void_p(_stream(stream))))
         return y
 
-    def elastic_residual(self, stream=None):
+    def elastic_residual(self, stream=None, precision="fp64"):
         r = torch.empty(2 * self.n_nodes, dtype=torch.float64, device=self.workspace.device)
         n2 = C.c_double()
-        B.check(self.lib.pf_op_elastic_residual(self.h, _ptr(r), C.byref(n2),
+        prec = B.PF_MIXED if precision == "mixed" else B.PF_FP64
+        B.check(self.lib.pf_op_elastic_residual(self.h, prec, _ptr(r), C.byref(n2),
                                                 C.c_void_p(_stream(stream))))
         return r, n2.value
 
-    def damage_gradient(self, stream=None):
+    def damage_gradient(self, stream=None, precision="fp64"):
         dev = self.workspace.device
         F = torch.empty(self.n_nodes, dtype=torch.float64, device=dev)
         Phi = torch.empty_like(F)
         act = torch.empty(self.n_nodes, dtype=torch.uint8, device=dev)
         n2 = C.c_double()
-        B.check(self.lib.pf_op_damage_gradient(self.h, _ptr(F), _ptr(Phi), _ptr(act), C.byref(n2),
-                                               C.c_void_p(_stream(stream))))
+        prec = B.PF_MIXED if precision == "mixed" else B.PF_FP64
+        B.check(self.lib.pf_op_damage_gradient(self.h, prec, _ptr(F), _ptr(Phi), _ptr(act),
+                                               C.byref(n2), C.c_void_p(_stream(stream))))
         return F, Phi, act, n2.value
 
     def damage_apply(self, x: torch.Tensor, stream=None) -> torch.Tensor:

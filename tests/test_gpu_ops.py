@@ -73,12 +73,14 @@ def test_elastic_residual(kind, nx, ny, thermal):
     uu[p.u_fixed] = p.u.ravel()[p.u_fixed]
     Fu, _ = fe.gradients(p.mat, p.geo, uu.reshape(-1, 2), alpha, dT)
     rref = np.where(~p.u_fixed, -Fu, 0.0)
-    r, n2 = g.elastic_residual()
-    r = r.cpu().numpy()
     K = fe.stiffness(p.mat, p.geo, alpha)
     scale = abs(K) @ np.abs(uu) + np.abs(fe.thermal_load(p.mat, p.geo, alpha, dT)) + 1e-300
-    assert np.all(np.abs(r - rref) <= 1e-12 * scale)
-    np.testing.assert_allclose(n2, rref @ rref, rtol=1e-10)
+    # FP64, and the double-float arithmetic of the mixed path: both within 1e-12 of the terms
+    for precision in ("fp64", "mixed"):
+        r, n2 = g.elastic_residual(precision=precision)
+        r = r.cpu().numpy()
+        assert np.all(np.abs(r - rref) <= 1e-12 * scale), precision
+        np.testing.assert_allclose(n2, rref @ rref, rtol=1e-10)
 
 
 @pytest.mark.parametrize("kind,nx,ny", [("right", 70, 19), ("crossed", 45, 37), ("right", 1, 1)])
@@ -104,19 +106,20 @@ def test_damage_operator_gradient_residual_active_set(kind, nx, ny, model):
     assert np.all(np.abs(y - H @ x) <= 1e-12 * scale)
     y32 = g.damage_apply(xd.float()).double().cpu().numpy()
     assert np.all(np.abs(y32 - H @ x) <= 2e-5 * scale)
-    F, Phi, act, n2 = g.damage_gradient()
-    F, Phi, act = F.cpu().numpy(), Phi.cpu().numpy(), act.cpu().numpy()
     Fref = H @ alpha + g0
     fscale = abs(H) @ np.abs(alpha) + np.abs(g0) + 1e-300
-    assert np.all(np.abs(F - Fref) <= 1e-12 * fscale)
     lo, hi = p.lower(), p.upper()
     Pref = mcp_residual(alpha, Fref, lo, hi, np.ones(alpha.size, dtype=bool))
-    assert np.all(np.abs(Phi - Pref) <= 1e-10 * fscale)
     aref = active_set(alpha, Fref, lo, hi, np.ones(alpha.size, dtype=bool), 1e-10)
-    # decisions agree wherever F is not within rounding of zero
-    clear = np.abs(Fref) > 1e-9 * fscale
-    np.testing.assert_array_equal(act.astype(bool)[clear], aref[clear])
-    np.testing.assert_allclose(n2, Pref @ Pref, rtol=1e-8)
+    for precision in ("fp64", "mixed"):  # FP64, and the mixed path's double-float
+        F, Phi, act, n2 = g.damage_gradient(precision=precision)
+        F, Phi, act = F.cpu().numpy(), Phi.cpu().numpy(), act.cpu().numpy()
+        assert np.all(np.abs(F - Fref) <= 1e-12 * fscale), precision
+        assert np.all(np.abs(Phi - Pref) <= 1e-10 * fscale)
+        # decisions agree wherever F is not within rounding of zero
+        clear = np.abs(Fref) > 1e-9 * fscale
+        np.testing.assert_array_equal(act.astype(bool)[clear], aref[clear])
+        np.testing.assert_allclose(n2, Pref @ Pref, rtol=1e-8)
 
 
 @pytest.mark.parametrize("kind,nx,ny", [("right", 70, 19), ("crossed", 45, 37)])

@@ -179,3 +179,20 @@ def test_single_block_tail_matches_grid_vcycle(n):
     for x, y in zip(r1, r0):
         np.testing.assert_allclose(x["energy"], y["energy"], rtol=1e-10, atol=1e-15)
         assert abs(x["cg_iters_u"] - y["cg_iters_u"]) <= max(2, 0.05 * y["cg_iters_u"])
+
+
+def test_bar_config_full_schedule_against_oracle():
+    """The 128 x 16 bar (Section 4.2) over its whole 20-step schedule, AM, FP64: every step's
+    energies at 1e-8 and the final fields at 1e-6 against the oracle.  The nucleation step picks
+    its branch by round-off in a perfectly symmetric bar, so both sides carry the same seed
+    column (alpha_prev = 1e-3 next to the middle)."""
+    w = W.bar(seed_column=True)
+    g, p, reps = _run_steps(w, w.loads, omega=1.0)
+    for rep, r in reps:
+        np.testing.assert_allclose(rep["energy"], r["energy"], rtol=1e-8, atol=1e-14)
+        assert rep["status"] == 0
+    _fields_close(g, p)
+    # elastic phase below t_c (no damage beyond the seed), then at step 14 a crack whose surface
+    # energy is about Gc H = 0.1 (Section 4.2)
+    assert reps[12][1]["energy"][1] < 1e-3 and p.alpha.max() > 0.99
+    assert abs(reps[13][0]["energy"][1] - 0.1) < 0.01
