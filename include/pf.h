@@ -115,8 +115,10 @@ typedef struct pf_load {
  *           displacement, so that a step whose damage does not move still solves for u).
  *   u_rtol: u-subproblem FP64 residual <= u_rtol * (largest residual seen in the load step).
  *   inner_rtol: relative tolerance of each inner FP32 CG solve (PF_MIXED).
- *   rs_rtol: damage subproblem ||Phi||_2 <= rs_rtol * (largest ||Phi||_2 seen in the load step)
- *           (Algorithm 4 termination).
+ *   rs_rtol: damage subproblem ||Phi||_2 <= rs_rtol * max(largest ||Phi||_2 seen in the load
+ *           step, size of the terms summed into E_alpha) (Algorithm 4 termination; the term size,
+ *           sqrt(n) (8/3) |T| (2 c3 + c2) with c3 = Gc/(c_w ell), c2 = 2 Gc/(c_w ell) for AT2, is
+ *           the scale at a load at the AT1 threshold, where the linear term cancels).
  *   am_forcing, am_forcing_max: inexact subproblem solves.  In AM iteration k the two
  *           tolerances above are raised to f_k = min(am_forcing_max, am_forcing * dalpha_{k-1})
  *           (dalpha_0 = infinity), so the subproblems are solved loosely while the damage moves

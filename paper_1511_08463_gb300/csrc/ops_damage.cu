@@ -70,7 +70,8 @@ static void dispatch(cudaStream_t s, const Grid& g, const Mat& m, int mode, bool
     case M_MASKED:
       return dot ? go<T, K, M_MASKED, true>(s, g, m, a) : go<T, K, M_MASKED, false>(s, g, m, a);
     case M_RESB: return go<T, K, M_RESB, false>(s, g, m, a);
-    case M_CHEB: return go<T, K, M_CHEB, false>(s, g, m, a);
+    case M_CHEB:
+      return dot ? go<T, K, M_CHEB, true>(s, g, m, a) : go<T, K, M_CHEB, false>(s, g, m, a);
   }
   if constexpr (sizeof(T) == 8) {
     if (mode == M_GRAD) return go<T, K, M_GRAD, false>(s, g, m, a);

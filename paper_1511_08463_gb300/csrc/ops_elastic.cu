@@ -82,7 +82,9 @@ static void dispatch(cudaStream_t s, const Grid& g, const Mat& m, int coef, int 
         return dot ? go<T, K, COEF_ELEM, M_MASKED, false, true>(s, g, m, a)
                    : go<T, K, COEF_ELEM, M_MASKED, false, false>(s, g, m, a);
       case M_RESB: return go<T, K, COEF_ELEM, M_RESB, false, false>(s, g, m, a);
-      case M_CHEB: return go<T, K, COEF_ELEM, M_CHEB, false, false>(s, g, m, a);
+      case M_CHEB:
+        return dot ? go<T, K, COEF_ELEM, M_CHEB, false, true>(s, g, m, a)
+                   : go<T, K, COEF_ELEM, M_CHEB, false, false>(s, g, m, a);
     }
   }
 }

@@ -406,8 +406,9 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
 
 template <class T>
 void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, const T* d,
-               T* xo, T* dout, double cd, double cr, const T* xc = nullptr) {
+               T* xo, T* dout, double cd, double cr, const T* xc = nullptr, int dot_slot = -1) {
   Level& L = s.lv[l];
+  const bool dot = dot_slot >= 0;
   if (phys == ELASTIC) {
     ElasticArgs<T> a{};
     if (xc) {
@@ -425,7 +426,8 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.y = xo;
     a.dout = dout;
     a.coarse = l;
-    launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_CHEB, false, false, a);
+    if (dot) a.slot = slot(s, dot_slot);
+    launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_CHEB, false, dot, a);
   } else {
     DamageArgs<T> a{};
     if (xc) {
@@ -443,7 +445,8 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
     a.y = xo;
     a.dout = dout;
     a.coarse = l;
-    launch_damage<T>(st, L.g, s.m, M_CHEB, false, a);
+    if (dot) a.slot = slot(s, dot_slot);
+    launch_damage<T>(st, L.g, s.m, M_CHEB, dot, a);
   }
 }
 
@@ -451,9 +454,10 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
 // spectrum by 1).  Starts from x (x0 == nullptr: from zero); result written to x.
 // xc (optional, not with from_zero): the coarse-grid correction, prolongated into x by the first
 // step as it reads x (x + P xc), which saves the separate prolongation launch.
+// dot_slot >= 0: the last step also reduces b . x_new into that scalar slot
 template <class T>
 void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool from_zero,
-            int steps, const T* xc = nullptr) {
+            int steps, const T* xc = nullptr, int dot_slot = -1) {
   LevelBuf<T>& B = s.lv[l].buf<T>();
   const int nc = phys == ELASTIC ? 2 : 1;
   const size_t nd = (size_t)nc * s.lv[l].g.n;
@@ -476,7 +480,8 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
       crk = 2.0 * rn / delta;
       rho = rn;
     }
-    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk, k == 0 ? xc : nullptr);
+    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk, k == 0 ? xc : nullptr,
+                 k == steps - 1 ? dot_slot : -1);
     // rotate buffers: new x becomes current; the old current x buffer is free for the next step
     T* ox = cx;
     cx = nx_;
@@ -561,12 +566,15 @@ void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x,
   tail_vcycle(st, nc, a, (size_t)off * sizeof(float));
 }
 
+// Returns true if dot_slot received b . x from the last level-0 smoothing step (false when the
+// single-block tail ran this level or no slot was asked for).
 template <class T>
-void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int deg) {
+bool vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int deg,
+            int dot_slot = -1) {
   if constexpr (std::is_same<T, float>::value) {
     if (l == tail_first(s, phys)) {
       launch_tail(s, st, phys, b, x, deg);
-      return;
+      return false;
     }
   }
   Level& L = s.lv[l];
@@ -576,10 +584,10 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
   if (l == nlev - 1) {
     if (L.dense && nlev > 1) {
       coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AEi : B.ADi, b, x);
-    } else {
-      smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * s.cdeg : deg);
+      return false;
     }
-    return;
+    smooth<T>(s, st, phys, l, b, x, true, nlev > 1 ? 8 * s.cdeg : deg, nullptr, dot_slot);
+    return dot_slot >= 0;
   }
   Level& C = s.lv[l + 1];
   LevelBuf<T>& BC = C.buf<T>();
@@ -590,19 +598,26 @@ void vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
                   phys == DAMAGE ? C.exclD : nullptr, l);
   vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
   // prolongation x += P x_c fused into the first post-smoothing step
-  smooth<T>(s, st, phys, l, b, x, false, dl, BC.x);
+  smooth<T>(s, st, phys, l, b, x, false, dl, BC.x, dot_slot);
+  return dot_slot >= 0;
 }
 
+// z = M r; with dot_slot >= 0, also r . z into that slot, computed by the preconditioner's last
+// level-0 kernel when it can (returns true) -- otherwise the caller reduces it itself
 template <class T>
-void precond(pf_sim& s, cudaStream_t st, int phys, const T* r, T* z, int deg) {
-  const int nc = phys == ELASTIC ? 2 : 1;
+bool precond(pf_sim& s, cudaStream_t st, int phys, const T* r, T* z, int deg, int dot_slot = -1) {
   if (s.nl_active == 1) {
     // single level: Chebyshev smoother alone
-    smooth<T>(s, st, phys, 0, r, z, true, deg);
-    (void)nc;
-    return;
+    smooth<T>(s, st, phys, 0, r, z, true, deg, nullptr, dot_slot);
+    return dot_slot >= 0;
   }
-  vcycle<T>(s, st, phys, 0, r, z, deg);
+  return vcycle<T>(s, st, phys, 0, r, z, deg, dot_slot);
+}
+// z = M r and r . z into the slot, fused when the preconditioner allows it
+template <class T>
+void precond_dot(pf_sim& s, cudaStream_t st, int phys, const T* r, T* z, int deg, size_t nd,
+                 int dot_slot) {
+  if (!precond<T>(s, st, phys, r, z, deg, dot_slot)) vec_dot<T>(st, r, z, nd, slot(s, dot_slot));
 }
 
 // set up the coefficients, l1 diagonals and the coarsest factorization of one operator
@@ -663,8 +678,7 @@ pf_status pcg_host(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, 
   if (relres) *relres = 0.0;
   if (rr0 == 0.0) return PF_OK;
   const double tol2 = rtol * rtol * rr0;
-  precond<T>(s, st, phys, K.r, K.z, deg);
-  vec_dot<T>(st, K.r, K.z, nd, slot(s, S_RZ0));
+  precond_dot<T>(s, st, phys, K.r, K.z, deg, nd, S_RZ0);
   cg_update_p<T>(st, K.p, K.z, nd, nullptr, nullptr);
   int cur = 0;
   double rr = rr0;
@@ -676,8 +690,7 @@ pf_status pcg_host(pf_sim& s, cudaStream_t st, int phys, const T* b, int maxit, 
     TRY(read_scalars(s, st, S_RR, 1, &rr));
     if (!(rr == rr)) return fail(PF_ENUMERIC, "CG breakdown (NaN residual)");
     if (rr <= tol2) break;
-    precond<T>(s, st, phys, K.r, K.z, deg);
-    vec_dot<T>(st, K.r, K.z, nd, slot(s, cur ? S_RZ0 : S_RZ1));
+    precond_dot<T>(s, st, phys, K.r, K.z, deg, nd, cur ? S_RZ0 : S_RZ1);
     cg_update_p<T>(st, K.p, K.z, nd, s.scal + (cur ? S_RZ0 : S_RZ1), s.scal + (cur ? S_RZ1 : S_RZ0));
     cur ^= 1;
   }
@@ -732,8 +745,7 @@ pf_status build_cg_graph(pf_sim& s, int phys, int deg) {
   own.cs = cs;
   CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   prof_set_capturing(true);
-  precond<T>(s, cs, phys, K.r, K.z, deg);
-  vec_dot<T>(cs, K.r, K.z, nd, slot(s, S_RZ1));
+  precond_dot<T>(s, cs, phys, K.r, K.z, deg, nd, S_RZ1);
   cg_update_p<T>(cs, K.p, K.z, nd, s.scal + S_RZ1, s.scal + S_RZ0);
   apply_op<T>(s, cs, phys, 0, K.p, K.Ap, true, S_PAP);
   cg_update_xr<T>(cs, K.x, K.r, K.p, K.Ap, nd, s.scal + S_RZ1, s.scal + S_PAP, slot(s, S_RR));
@@ -895,6 +907,7 @@ pf_status u_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_step_r
 // ---------------------------------------------------------------------------------------------
 // damage subproblem: Algorithm 4 on the box [alpha_prev, 1]
 // ---------------------------------------------------------------------------------------------
+// out[0] = ||Phi||^2, out[1] = ||F_N||^2
 pf_status grad_at(pf_sim& s, cudaStream_t st, const double* x, double zeta, double* F, double* Phi,
                   double* rhs, uint8_t* act, double out[2]) {
   DamageArgs<double> a{};
@@ -951,7 +964,13 @@ pf_status alpha_solve(pf_sim& s, cudaStream_t st, const pf_solver_opts& o, pf_st
   double phi2 = v[0];
   double phi0 = sqrt(phi2);
   s.phi_scale = std::max(s.phi_scale, phi0);
-  const double tol = o.rs_rtol * s.phi_scale;
+  // relative to the largest ||Phi|| of the load step, and to the size of the gradient's terms:
+  // at a load at the AT1 damage threshold the linear term (c3 - q_T) |T| / 3 cancels, and what is
+  // left of F is the error the u-subproblem's tolerance leaves in q (its largest ||Phi|| is then
+  // no scale).  The terms' size per node is about (c3 + q_T + c2) |T| / 3 over the node's (up
+  // to 8) elements, with q_T ~ c3 at the threshold.
+  const double term = 8.0 * g.area * (2.0 * s.m.c3 + s.m.c2) / 3.0;
+  const double tol = o.rs_rtol * std::max(s.phi_scale, sqrt(double(n)) * term);
   const double c_armijo = 1e-4;
   int it = 0;
   for (;;) {

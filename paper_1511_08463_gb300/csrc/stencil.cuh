@@ -47,8 +47,11 @@ inline Consts<T> make_consts(const Grid& g, const Mat& m) {
 // ----------------------------------------------------------------------------------------------
 // generic tile kernel
 // ----------------------------------------------------------------------------------------------
+// FP32 elasticity and damage operators are compiled for full occupancy (2048 threads per SM, at
+// most 32 registers per thread)
 template <class Op, int TYV = TY>
-__global__ void __launch_bounds__(TX* TYV) stencil_kernel(Op op) {
+__global__ void __launch_bounds__(TX* TYV, Op::FULL_OCC ? 2048 / (TX * TYV) : 1)
+    stencil_kernel(Op op) {
   pdl_enter();
   using V = typename Op::V;
   using R = typename Op::R;
@@ -60,8 +63,12 @@ __global__ void __launch_bounds__(TX* TYV) stencil_kernel(Op op) {
   __shared__ V sv[TYV + 2][TX + 2];
   __shared__ V sc[NC][TX + 1];
   // element records stored component-major: consecutive cells -> consecutive words, so both the
-  // record writes and the gathers are free of shared-memory bank conflicts
-  __shared__ ET se[NRC][NE][TYV + 1][TX + 1];
+  // record writes and the gathers are free of shared-memory bank conflicts.  (A record-major
+  // layout with one 16-byte word per FP32 record needs fewer instructions but four shared-memory
+  // wavefronts per warp access instead of three; it measured slower.)
+  constexpr bool VEC4 = false;
+  __shared__ typename std::conditional<VEC4, float4, ET>::type
+      se[VEC4 ? 1 : NRC][NE][TYV + 1][TX + 1];
   const Grid& g = op.g;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TYV;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -83,8 +90,12 @@ __global__ void __launch_bounds__(TX* TYV) stencil_kernel(Op op) {
   }
   __syncthreads();
   auto put = [&](int t, int lj, int li, const R& r) {
+    if constexpr (VEC4) {
+      se[0][t][lj][li] = make_float4(r.c[0], r.c[1], r.c[2], NRC == 4 ? r.c[NRC - 1] : 0.f);
+    } else {
 #pragma unroll
-    for (int c = 0; c < NRC; ++c) se[c][t][lj][li] = r.c[c];
+      for (int c = 0; c < NRC; ++c) se[c][t][lj][li] = r.c[c];
+    }
   };
   for (int s = tid; s < (TX + 1) * (TYV + 1); s += TX * TYV) {
     int li = s % (TX + 1), lj = s / (TX + 1);
@@ -92,22 +103,31 @@ __global__ void __launch_bounds__(TX* TYV) stencil_kernel(Op op) {
     bool valid = ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny;
     V v00 = sv[lj][li], v10 = sv[lj][li + 1], v01 = sv[lj + 1][li], v11 = sv[lj + 1][li + 1];
     int cell = cj * g.nx + ci;
+    const typename Op::Cell cd = op.cell(valid, cell);  // the cell's coefficients, one load
     if constexpr (KIND == CROSSED) {
       V c = sc[lj][li];
-      put(0, lj, li, op.template element<0>(valid, cell, cj, v00, v10, c));
-      put(1, lj, li, op.template element<1>(valid, cell, cj, v10, v11, c));
-      put(2, lj, li, op.template element<2>(valid, cell, cj, v11, v01, c));
-      put(3, lj, li, op.template element<3>(valid, cell, cj, v01, v00, c));
+      put(0, lj, li, op.template element<0>(valid, cell, cj, cd, v00, v10, c));
+      put(1, lj, li, op.template element<1>(valid, cell, cj, cd, v10, v11, c));
+      put(2, lj, li, op.template element<2>(valid, cell, cj, cd, v11, v01, c));
+      put(3, lj, li, op.template element<3>(valid, cell, cj, cd, v01, v00, c));
     } else {
-      put(0, lj, li, op.template element<0>(valid, cell, cj, v00, v10, v11));
-      put(1, lj, li, op.template element<1>(valid, cell, cj, v00, v11, v01));
+      put(0, lj, li, op.template element<0>(valid, cell, cj, cd, v00, v10, v11));
+      put(1, lj, li, op.template element<1>(valid, cell, cj, cd, v00, v11, v01));
     }
   }
   __syncthreads();
   auto get = [&](int t, int lj, int li) {
     R r;
+    if constexpr (VEC4) {
+      const float4 v = se[0][t][lj][li];
+      r.c[0] = v.x;
+      r.c[1] = v.y;
+      r.c[2] = v.z;
+      if constexpr (NRC == 4) r.c[NRC - 1] = v.w;
+    } else {
 #pragma unroll
-    for (int c = 0; c < NRC; ++c) r.c[c] = se[c][t][lj][li];
+      for (int c = 0; c < NRC; ++c) r.c[c] = se[c][t][lj][li];
+    }
     return r;
   };
 
@@ -241,6 +261,26 @@ __device__ __forceinline__ C gsum(C x, C y, C z) {
     return C(a) * x + C(b) * y + C(c) * z;
   }
 }
+// The NE per-element coefficients of a cell (cell-major arrays), as the arithmetic type: one
+// 16- or 8-byte load for FP32 (the arrays start on 256-byte boundaries)
+template <class C, int NE, class T>
+__device__ __forceinline__ void load_cell_coefs(const T* p, int cell, C (&w)[NE]) {
+  if constexpr (std::is_same<T, float>::value && NE == 4) {
+    const float4 v = reinterpret_cast<const float4*>(p)[cell];
+    w[0] = to_c<C>(v.x);
+    w[1] = to_c<C>(v.y);
+    w[2] = to_c<C>(v.z);
+    w[3] = to_c<C>(v.w);
+  } else if constexpr (std::is_same<T, float>::value && NE == 2) {
+    const float2 v = reinterpret_cast<const float2*>(p)[cell];
+    w[0] = to_c<C>(v.x);
+    w[1] = to_c<C>(v.y);
+  } else {
+#pragma unroll
+    for (int t = 0; t < NE; ++t) w[t] = to_c<C>(p[cell * NE + t]);
+  }
+}
+
 // storage value of a computed one
 template <class T, class C>
 __device__ __forceinline__ T to_t(C v) {
@@ -253,13 +293,24 @@ __device__ __forceinline__ T to_t(C v) {
 template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT, class C = T>
 struct ElasticOp {
   using Scalar = T;
+  static constexpr bool FULL_OCC = sizeof(T) == 4;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
   static constexpr bool RED_MAX = false;
   // per-thread partial sums in the operator's precision (FP64 for double-float)
   using RT = typename std::conditional<std::is_same<C, dfloat>::value, double, C>::type;
-  struct V {
+  static constexpr int NE_ = elems_per_cell(KIND_);
+  // a staged node: displacement, and the damage when the coefficient is computed from it
+  struct VA {
     C ux, uy, a;
+  };
+  struct __align__(2 * sizeof(C)) VE {
+    C ux, uy;
+  };
+  using V = typename std::conditional<COEF == COEF_ALPHA, VA, VE>::type;
+  // per-cell data of the records loop: the stored element coefficients (COEF_ELEM)
+  struct Cell {
+    C w[COEF == COEF_ELEM ? NE_ : 1];
   };
   using ET = C;
   static constexpr int NRC = 3;
@@ -274,8 +325,18 @@ struct ElasticOp {
   Consts<C> cs;
   ElasticArgs<T> args;
 
-  __device__ static V zero() { return V{C(0), C(0), C(0)}; }
+  __device__ static V zero() {
+    V v{};
+    return v;
+  }
   __device__ static Acc acc0() { return Acc{C(0), C(0), C(0), C(0)}; }
+
+  __device__ Cell cell(bool valid, int c) const {
+    Cell d{};
+    if constexpr (COEF == COEF_ELEM)
+      if (valid) load_cell_coefs<C>(args.coef, c, d.w);
+    return d;
+  }
 
   __device__ V load(int node, int X2, int Y2) const {
     V v;
@@ -295,21 +356,32 @@ struct ElasticOp {
       if (is_fixed(g, X2, Y2, 0)) v.ux = C(0);
       if (is_fixed(g, X2, Y2, 1)) v.uy = C(0);
     }
-    v.a = COEF == COEF_ALPHA ? to_c<C>(args.alpha[node]) : C(0);
+    if constexpr (COEF == COEF_ALPHA) v.a = to_c<C>(args.alpha[node]);
     return v;
   }
 
+  // one element with its own scalar coefficient load (callers whose coefficient array carries
+  // no alignment guarantee, e.g. the single-block tail's shared-memory copy)
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
+    Cell d{};
+    if constexpr (COEF == COEF_ELEM)
+      if (valid) d.w[t] = to_c<C>(args.coef[cell * NE_ + t]);
+    return element<t>(valid, cell, cj, d, n0, n1, n2);
+  }
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const Cell& cd, const V& n0, const V& n1,
+                       const V& n2) const {
     if (!valid) return R{{C(0), C(0), C(0)}};
     constexpr int NE = elems_per_cell(KIND);
     constexpr int a0 = gx(KIND, t, 0), a1 = gx(KIND, t, 1), a2 = gx(KIND, t, 2);
     constexpr int b0 = gy(KIND, t, 0), b1 = gy(KIND, t, 1), b2 = gy(KIND, t, 2);
     C w;
-    if (COEF == COEF_ALPHA)
+    if constexpr (COEF == COEF_ALPHA)
       w = abar3<C>(n0.a, n1.a, n2.a, cs.k_ell) * cs.area;
     else
-      w = to_c<C>(args.coef[cell * NE + t]) * cs.area;
+      w = cd.w[t] * cs.area;
+    (void)NE;
     const C ihx = cs.ihx, ihy = cs.ihy;
     C sx = gsum<a0, a1, a2>(n0.ux, n1.ux, n2.ux);
     C sy = gsum<b0, b1, b2>(n0.uy, n1.uy, n2.uy);
@@ -369,7 +441,10 @@ struct ElasticOp {
         T dx = f0 ? T(0) : args.cd * p.x + args.cr * di.x * rx;
         T dy = f1 ? T(0) : args.cd * p.y + args.cr * di.y * ry;
         st_pair(args.dout, node, dx, dy);
-        st_pair(args.y, node, own.ux + dx, own.uy + dy);
+        const T yx = own.ux + dx, yy = own.uy + dy;
+        st_pair(args.y, node, yx, yy);
+        // the preconditioner's last step: r.z of the CG, with b = r and the new x = z
+        if (DOT) red[0] += b.x * yx + b.y * yy;
       }
     }
   }
@@ -406,6 +481,7 @@ struct DamageArgs {
 template <class T, int KIND_, int MODE, bool DOT, class C = T>
 struct DamageOp {
   using Scalar = T;
+  static constexpr bool FULL_OCC = sizeof(T) == 4;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
   static constexpr bool RED_MAX = false;
@@ -413,6 +489,10 @@ struct DamageOp {
   using RT = typename std::conditional<DF, double, C>::type;
   struct V {
     C p;
+  };
+  static constexpr int NE_ = elems_per_cell(KIND_);
+  struct Cell {  // the cell's element weights
+    C w[NE_];
   };
   using ET = C;
   static constexpr int NRC = 4;
@@ -429,6 +509,12 @@ struct DamageOp {
 
   __device__ static V zero() { return V{C(0)}; }
   __device__ static Acc acc0() { return Acc{C(0), C(0), C(0), C(0)}; }
+
+  __device__ Cell cell(bool valid, int c) const {
+    Cell d{};
+    if (valid) load_cell_coefs<C>(args.w, c, d.w);
+    return d;
+  }
 
   __device__ double upper(int X2, int Y2, double l) const {
     return is_fixed(g, X2, Y2, 2) ? l : 1.0;
@@ -454,14 +540,22 @@ struct DamageOp {
     return v;
   }
 
+  // one element with its own scalar weight load (callers whose weight array carries no alignment
+  // guarantee, e.g. the single-block tail's shared-memory copy)
   template <int t>
   __device__ R element(bool valid, int cell, int cj, const V& n0, const V& n1, const V& n2) const {
+    Cell d{};
+    if (valid) d.w[t] = to_c<C>(args.w[cell * NE_ + t]);
+    return element<t>(valid, cell, cj, d, n0, n1, n2);
+  }
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const Cell& cd, const V& n0, const V& n1,
+                       const V& n2) const {
     if (!valid) return R{{C(0), C(0), C(0), C(0)}};
-    constexpr int NE = elems_per_cell(KIND);
     constexpr int a0 = gx(KIND, t, 0), a1 = gx(KIND, t, 1), a2 = gx(KIND, t, 2);
     constexpr int b0 = gy(KIND, t, 0), b1 = gy(KIND, t, 1), b2 = gy(KIND, t, 2);
     const C area = cs.area;
-    C wt = to_c<C>(args.w[cell * NE + t]);
+    C wt = cd.w[t];
     C qT = wt;
     if (MODE == M_GRAD || MODE == M_TRIAL) wt = wt + cs.c2;
     C me = wt * area * C(1.0 / 12.0);
@@ -520,9 +614,11 @@ struct DamageOp {
         if (DOT) red[0] += r * r;
       } else if (MODE == M_CHEB) {
         T dp = args.d ? args.d[node] : T(0);
-        T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (args.b[node] - f);
+        const T bn = args.b[node];
+        T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (bn - f);
         args.dout[node] = dn;
         args.y[node] = own.p + dn;
+        if (DOT) red[0] += bn * (own.p + dn);  // r.z of the CG (see ElasticOp)
       }
     }
   }
@@ -553,6 +649,7 @@ struct CouplingArgs {
 template <class T, int KIND_, bool TRANSPOSE>
 struct CouplingOp {
   using Scalar = T;
+  static constexpr bool FULL_OCC = false;
   static constexpr int KIND = KIND_;
   static constexpr int NR = 0;
   static constexpr bool RED_MAX = false;
@@ -589,6 +686,14 @@ struct CouplingOp {
     v.uy = args.u[2 * node + 1];
     v.a = args.alpha[node];
     return v;
+  }
+
+  struct Cell {};
+  __device__ Cell cell(bool, int) const { return Cell{}; }
+  template <int t>
+  __device__ R element(bool valid, int cell, int cj, const Cell&, const V& n0, const V& n1,
+                       const V& n2) const {
+    return element<t>(valid, cell, cj, n0, n1, n2);
   }
 
   template <int t>

@@ -25,7 +25,7 @@ template <int KIND>
 struct TailOp<KIND, 2> {
   using Op = ElasticOp<float, KIND, COEF_ELEM, M_APPLY, false, false>;
   static __device__ typename Op::V val(const float* x, int node) {
-    return typename Op::V{x[2 * node], x[2 * node + 1], 0.f};
+    return typename Op::V{x[2 * node], x[2 * node + 1]};
   }
   static __device__ void result(const Op& op, const typename Op::Acc& a, const typename Op::V&,
                                 float* f) {

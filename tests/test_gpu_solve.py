@@ -196,3 +196,22 @@ def test_bar_config_full_schedule_against_oracle():
     # energy is about Gc H = 0.1 (Section 4.2)
     assert reps[12][1]["energy"][1] < 1e-3 and p.alpha.max() > 0.99
     assert abs(reps[13][0]["energy"][1] - 0.1) < 0.01
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_load_exactly_at_damage_threshold_converges(precision):
+    """A load step exactly at the AT1 critical load of the bar (t = t_c: the linear term of the
+    damage gradient cancels, so what is left of it is the u-solve's error): the damage solve's
+    tolerance follows the size of the gradient's terms, and the step converges like its
+    neighbours; the bar is still undamaged (elastic energy 1/2 E' (t/L)^2 L H = 0.375)."""
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    w = W.bar(nx=128, ny=16, n_steps=30)  # t_20 = 1.5 t_c 20 / 30 = t_c
+    g = S.Sim(w)
+    o = S.make_opts(omega=1.0, precision=precision, am_maxit=500)
+    for (t, dT) in w.loads[:20]:
+        rep = g.load_step(t, dT, o)
+        assert rep["status"] == 0 and rep["am_iters"] < 50
+        assert rep["alpha_notconv"] == 0
+    assert abs(rep["energy"][0] - 0.375) < 1e-4 and rep["energy"][1] < 1e-6
