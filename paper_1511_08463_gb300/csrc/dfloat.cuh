@@ -54,6 +54,20 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
   df_quick_two_sum(p, e, s, r);
   return dfloat(s, r);
 }
+// square root of a non-negative value: the FP32 root of the high part, corrected by one Newton
+// step whose residual x - s^2 is formed exactly (TwoProduct)
+__device__ __forceinline__ dfloat df_sqrt(dfloat x) {
+  if (!(x.hi > 0.f)) return dfloat(0.f, 0.f);
+  const float s = sqrtf(x.hi);
+  const float p = s * s;
+  const float pe = fmaf(s, s, -p);
+  const float r = ((x.hi - p) - pe) + x.lo;
+  float h, l;
+  df_quick_two_sum(s, r / (s + s), h, l);
+  return dfloat(h, l);
+}
+__device__ __forceinline__ bool df_positive(dfloat a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+__device__ __forceinline__ bool df_negative(dfloat a) { return a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f); }
 __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
 __device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
 __device__ __forceinline__ dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }

@@ -587,10 +587,24 @@ struct DamageOp {
       else xv = double(own.p);
       const double F = to_t<double>(f);
       double l = args.lo[node], h = upper(X2, Y2, l);
-      double ph = mcp_phi(xv, F, l, h);
+      double ph;
+      bool fpos, fneg;
+      if constexpr (DF) {
+        // the nested Fischer-Burmeister function in double-float; the distances to the bounds
+        // are exact FP64 differences, F the double-float sum itself
+        const dfloat a = dfloat(xv - l), b = dfloat(h - xv), mf = -f;
+        const dfloat psi = df_sqrt(b * b + mf * mf) - b - mf;
+        ph = double(df_sqrt(a * a + psi * psi) - a - psi);
+        fpos = df_positive(f);
+        fneg = df_negative(f);
+      } else {
+        ph = mcp_phi(xv, F, l, h);
+        fpos = F > 0.0;
+        fneg = F < 0.0;
+      }
       // eq. reducedis with both bounds; a single-point box counts as lower-active
-      const bool lower = (h - l <= args.zeta) || (xv <= l + args.zeta && F > 0.0);
-      const bool upper = !lower && (xv >= h - args.zeta && F < 0.0);
+      const bool lower = (h - l <= args.zeta) || (xv <= l + args.zeta && fpos);
+      const bool upper = !lower && (xv >= h - args.zeta && fneg);
       const bool active = lower || upper;
       args.y[node] = T(F);
       args.dout[node] = T(ph);

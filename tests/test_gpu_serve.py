@@ -111,3 +111,30 @@ def test_solve_batch_concurrent_equals_sequential():
         np.testing.assert_array_equal(ub, u)
         np.testing.assert_array_equal(ab, a)
         assert r["energy"] == r1[0]["energy"]
+
+
+def test_served_jobs_match_oracle():
+    """Jobs that ran through the serving loop, next to each other, against the oracle's
+    Algorithm 2 on the same schedules: energies at every load step, fields at the end."""
+    need_gpu()
+    from oracle import am
+    from oracle.problem import Problem
+    from paper_1511_08463_gb300 import sim as S
+
+    from .gpu_util import rel_max, tight_opts
+
+    jobs = [W.notched_square(n=16, n_steps=8, t_max=1.6), W.bar(nx=64, ny=8, n_steps=6)]
+    srv = S.Server(4 * sum(S.Server.footprint(w) for w in jobs), workers=2)
+    ids = [srv.submit(w, opts=tight_opts(S, omega=w.omega), arrival=0.0) for w in jobs]
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    for w, r in zip(jobs, res):
+        assert r["status"] == 0 and r["steps_done"] == len(w.loads)
+        p = Problem(w)
+        for (t, dT), rep in zip(w.loads, r["reports"]):
+            o = am.load_step(p, t, dT, omega=w.omega, tol=1e-10, maxit=5000)
+            assert o["status"] == "converged"
+            np.testing.assert_allclose(rep["energy"], o["energy"], rtol=1e-8, atol=1e-14)
+        assert rel_max(r["u"], p.u) <= 1e-6
+        assert np.abs(r["alpha"] - p.alpha).max() <= 1e-6
+    assert res[0]["alpha"].max() > 0.5  # the notched job grew a crack
