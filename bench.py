@@ -52,7 +52,7 @@ def select_steps(nsched: int, first: int, k: int, growth) -> list:
     m = k - len(g)
     pick = set()
     for i in range(m):
-        pick.add(rest[int(round(i * (len(rest) - 1) / max(m - 1, 1)))] if m > 1 else rest[len(rest) // 2])
+        pick.add(rest[int(round(i * (len(rest) - 1) / max(m - 1, 1)))] if m > 1 else rest[0])
     for s in rest:  # rounding may have picked one twice
         if len(pick) >= m:
             break
@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--algo", choices=["ORAM", "ORAM_N"], default="ORAM",
                     help="ORAM (Algorithm 2) or ORAM-N (Algorithm 3)")
+    ap.add_argument("--growth-steps", default=",".join(map(str, GROWTH_STEPS)),
+                    help="comma-separated load steps always timed ('' : none; then one timed "
+                         "step is the first after the warm-up)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="damage-growth steps repeated in plain FP64 (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -582,7 +585,8 @@ def run_ours(args):
     # (select_steps).  A timed step: copy the state in from pinned host memory (e2e only), the
     # load step, copy the state back (e2e only).  value: sum of the device-event intervals around
     # the timed load steps alone (state resident); e2e: events around copy-in, step and copy-out.
-    timed = select_steps(nsched, W0, K, GROWTH_STEPS)
+    growth = tuple(int(x) for x in args.growth_steps.split(",") if x.strip())
+    timed = select_steps(nsched, W0, K, growth)
     last = max(timed)
     fp64_at = [k - 1 for k in FP64_STEPS if W0 <= k - 1 <= last] or [timed[0]]
     n = sim.n_nodes
@@ -737,7 +741,7 @@ def run_ours(args):
                 "mesh": f"{args.size}x{args.size} crossed P1", "dofs": n_dofs,
                 "load_steps": (f"{len(timed)} timed of steps {W0 + 1}-{last + 1} of {nsched} "
                                f"(t up to {w.loads[-1][0]}): {[k + 1 for k in timed]}; the "
-                               f"damage-growth steps {list(GROWTH_STEPS)} are always timed"),
+                               f"damage-growth steps {list(growth)} are always timed"),
                 "precision": args.precision, "parallelism": f"replicas x{world}",
                 "cuda_graphs": not args.no_graphs, "am_maxit": AM_MAXIT,
                 "l2": f"inputs larger than L2: resident state + work buffers "

@@ -143,7 +143,7 @@ typedef struct pf_solver_opts {
                             * l1-Jacobi Chebyshev smoother as preconditioner).  A coarsest level in
                             * use that is not the mesh's coarsest (dense solve) is smoothed with
                             * 8 * mg_degree steps. */
-  int32_t mg_degree;       /* Chebyshev smoothing steps per pre/post smoothing */
+  int32_t mg_degree;       /* Chebyshev smoothing steps per pre/post smoothing (1..16) */
   double switch_tol, newton_rtol;
   int32_t newton_maxit, minres_maxit;
   double minres_rtol;
@@ -155,7 +155,7 @@ typedef struct pf_solver_opts {
                             * SM's shared memory run as a single thread block; 0: one grid per
                             * step on every level */
   int32_t mg_coarse_degree; /* Chebyshev steps per smoothing on the coarse levels (0 (default):
-                             * mg_degree) */
+                             * mg_degree; at most 16) */
   int32_t omega_rule;      /* damage over-relaxation step (Algorithm 2): 0 (default) the
                             * recursive midpoint rule of Section 2.1 (omega, (1+omega)/2, ... until
                             * the update stays in the box); 1: always omega, then projection onto

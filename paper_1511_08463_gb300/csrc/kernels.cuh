@@ -112,14 +112,21 @@ struct TailLevel {
   const uint8_t* excl;   // damage: excluded nodes (device); elastic: null
   int ox, oxn, ob, od, odi, oc, oe;  // shared-memory offsets, in floats (oe: flag bytes)
 };
+constexpr int MAX_CHEB = 16;  // Chebyshev steps per smoothing (pf_solver_opts degrees)
 struct TailArgs {
-  int nl, deg, dense, coarse_steps;  // levels in the tail; smoothing steps; dense coarsest?
+  int nl, deg;                       // levels in the tail (ending in the dense solve); steps
   int deg0;                          // smoothing steps on the tail's first level
   int first_level;                   // hierarchy index of that level (launch accounting)
   int orec;                          // shared-memory offset of the element records, in floats
+  int dense_slices;                  // column ranges of the dense solve (its partial sums use
+                                     // the record area: dense_slices * n floats)
   const float* Ainv;                 // coarsest inverse (dense)
   const float* b_in;                 // right-hand side on the tail's first level (device)
+  const float* rf;                   // if set, b_in is not read: the right-hand side is the
+  Grid gf;                           // restriction of this residual on the finer grid gf
   float* x_out;                      // V-cycle result on that level (device)
+  float cheb_cd[MAX_CHEB], cheb_cr[MAX_CHEB];  // coefficients of Chebyshev step k, as the
+                                               // grid-wide smoother rounds them
   TailLevel L[MAX_TAIL];
 };
 size_t tail_smem_limit();  // dynamic shared memory available to the tail kernel (0: none)

@@ -66,8 +66,36 @@ __device__ __forceinline__ T fget(const Grid& gf, const T* v, bool centre, int i
   return v[(gf.nv + j * gf.nx + i) * ncomp + c];
 }
 
-// b_c(node) = (P^T r_f)(node) for every component: P1 interpolation weights 1 at the coincident
-// fine vertex and 1/2 at its fine neighbours; zero on prescribed and excluded coarse dofs.
+// (P^T r_f)(node), component c, at coarse doubled coordinates (X2, Y2): P1 interpolation
+// weights 1 at the coincident fine vertex and 1/2 at its fine neighbours.
+template <class T>
+__device__ __forceinline__ T restrict_value(const Grid& gf, int ncomp, const T* rf, int X2, int Y2,
+                                            int c) {
+  T acc;
+  if ((X2 & 1) == 0) {  // coarse vertex (I, J) = fine vertex (2I, 2J)
+    int i = X2, j = Y2;  // fine vertex indices 2I, 2J
+    acc = fget(gf, rf, false, i, j, c, ncomp);
+    T h = fget(gf, rf, false, i - 1, j, c, ncomp) + fget(gf, rf, false, i + 1, j, c, ncomp) +
+          fget(gf, rf, false, i, j - 1, c, ncomp) + fget(gf, rf, false, i, j + 1, c, ncomp);
+    if (gf.kind == RIGHT) {
+      h += fget(gf, rf, false, i + 1, j + 1, c, ncomp) + fget(gf, rf, false, i - 1, j - 1, c, ncomp);
+    } else {
+      h += fget(gf, rf, true, i, j, c, ncomp) + fget(gf, rf, true, i - 1, j, c, ncomp) +
+           fget(gf, rf, true, i, j - 1, c, ncomp) + fget(gf, rf, true, i - 1, j - 1, c, ncomp);
+    }
+    acc += T(0.5) * h;
+  } else {  // coarse centre (I, J) = fine vertex (2I+1, 2J+1)
+    int I = X2 / 2, J = Y2 / 2;
+    acc = fget(gf, rf, false, 2 * I + 1, 2 * J + 1, c, ncomp);
+    T h = fget(gf, rf, true, 2 * I, 2 * J, c, ncomp) + fget(gf, rf, true, 2 * I + 1, 2 * J, c, ncomp) +
+          fget(gf, rf, true, 2 * I, 2 * J + 1, c, ncomp) +
+          fget(gf, rf, true, 2 * I + 1, 2 * J + 1, c, ncomp);
+    acc += T(0.5) * h;
+  }
+  return acc;
+}
+
+// b_c(node) = (P^T r_f)(node) for every component; zero on prescribed and excluded coarse dofs.
 template <class T>
 __device__ __forceinline__ void restrict_node(const Grid& gf, const Grid& gc, int ncomp,
                                               int comp_base, const T* rf, T* bc,
@@ -75,27 +103,7 @@ __device__ __forceinline__ void restrict_node(const Grid& gf, const Grid& gc, in
   int X2, Y2;
   node_coords(gc, node, X2, Y2);
   for (int c = 0; c < ncomp; ++c) {
-    T acc;
-    if ((X2 & 1) == 0) {  // coarse vertex (I, J) = fine vertex (2I, 2J)
-      int i = X2, j = Y2;  // fine vertex indices 2I, 2J
-      acc = fget(gf, rf, false, i, j, c, ncomp);
-      T h = fget(gf, rf, false, i - 1, j, c, ncomp) + fget(gf, rf, false, i + 1, j, c, ncomp) +
-            fget(gf, rf, false, i, j - 1, c, ncomp) + fget(gf, rf, false, i, j + 1, c, ncomp);
-      if (gf.kind == RIGHT) {
-        h += fget(gf, rf, false, i + 1, j + 1, c, ncomp) + fget(gf, rf, false, i - 1, j - 1, c, ncomp);
-      } else {
-        h += fget(gf, rf, true, i, j, c, ncomp) + fget(gf, rf, true, i - 1, j, c, ncomp) +
-             fget(gf, rf, true, i, j - 1, c, ncomp) + fget(gf, rf, true, i - 1, j - 1, c, ncomp);
-      }
-      acc += T(0.5) * h;
-    } else {  // coarse centre (I, J) = fine vertex (2I+1, 2J+1)
-      int I = X2 / 2, J = Y2 / 2;
-      acc = fget(gf, rf, false, 2 * I + 1, 2 * J + 1, c, ncomp);
-      T h = fget(gf, rf, true, 2 * I, 2 * J, c, ncomp) + fget(gf, rf, true, 2 * I + 1, 2 * J, c, ncomp) +
-            fget(gf, rf, true, 2 * I, 2 * J + 1, c, ncomp) +
-            fget(gf, rf, true, 2 * I + 1, 2 * J + 1, c, ncomp);
-      acc += T(0.5) * h;
-    }
+    T acc = restrict_value(gf, ncomp, rf, X2, Y2, c);
     if (is_fixed(gc, X2, Y2, comp_base + c) || (excl_c && excl_c[node])) acc = T(0);
     bc[node * ncomp + c] = acc;
   }

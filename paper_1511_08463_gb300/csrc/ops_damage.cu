@@ -11,7 +11,7 @@ static double damage_bytes(const Grid& g, int mode, const DamageArgs<T>& a) {
   switch (mode) {
     case M_APPLY: node = 2 * t; break;
     case M_MASKED: node = 2 * t; break;
-    case M_RESB: node = 3 * t; break;
+    case M_RESB: node = (a.x0b ? 4 : 3) * t; break;  // x, b, r (x0b: b, dinv, r, x written)
     case M_CHEB: node = ((a.x ? 1 : 0) + (a.d ? 1 : 0) + 4) * t; break;  // b, dinv, y, d' (+ x, d)
     case M_GRAD: node = 5 * t + 1; break;
     case M_TRIAL: node = 7 * t + 1; break;
@@ -52,13 +52,13 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>&
       return;
     }
   }
+  const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED : M == M_RESB ? KC_DM_RESB
+                 : M == M_CHEB ? KC_DM_CHEB : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;
   DamageOp<T, K, M, D> op;
   op.g = g;
   op.m = m;
   op.cs = make_consts<T>(g, m);
   op.args = a;
-  const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED : M == M_RESB ? KC_DM_RESB
-                 : M == M_CHEB ? KC_DM_CHEB : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;
   launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse), damage_bytes<T>(g, M, a));
 }
 

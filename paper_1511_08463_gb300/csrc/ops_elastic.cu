@@ -11,7 +11,7 @@ static double elastic_bytes(const Grid& g, int coef, int mode, const ElasticArgs
   switch (mode) {
     case M_APPLY:
     case M_MASKED: node = 4 * t; break;
-    case M_RESB: node = 6 * t; break;
+    case M_RESB: node = (a.x0b ? 8 : 6) * t; break;  // x, b, r (x0b: b, dinv, r, x written)
     case M_RESID: node = 4 * t; break;
     case M_CHEB: node = ((a.x ? 2 : 0) + (a.d ? 2 : 0) + 8) * t; break;  // b, dinv, y, d' (+ x, d)
   }
@@ -50,13 +50,13 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>
       return;
     }
   }
+  const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
+                 : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;
   ElasticOp<T, K, C, M, E, D> op;
   op.g = g;
   op.m = m;
   op.cs = make_consts<T>(g, m);
   op.args = a;
-  const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
-                 : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;
   launch_op(s, op, kclass(base, sizeof(T) == 8, a.coarse), elastic_bytes<T>(g, C, M, a));
 }
 

@@ -380,12 +380,22 @@ void apply_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* x, T* y, boo
   }
 }
 
+// r = b - A x.  x0 > 0: x is not read but is the single Chebyshev step from zero, x0 D^-1 b,
+// formed on the fly and written to x.
 template <class T>
-void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, T* r) {
+void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, T* r,
+                 double x0 = 0.0) {
   Level& L = s.lv[l];
   if (phys == ELASTIC) {
     ElasticArgs<T> a{};
-    a.x = x;
+    if (x0 > 0.0) {
+      a.x0b = 1;
+      a.c0 = T(x0);
+      a.dinv = L.buf<T>().dinvE;
+      a.dout = x;
+    } else {
+      a.x = x;
+    }
     a.alpha = alpha_of<T>(s);
     a.coef = L.buf<T>().coefE;
     a.b = b;
@@ -394,7 +404,14 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
     launch_elastic<T>(st, L.g, s.m, COEF_ELEM, M_RESB, false, false, a);
   } else {
     DamageArgs<T> a{};
-    a.x = x;
+    if (x0 > 0.0) {
+      a.x0b = 1;
+      a.c0 = T(x0);
+      a.dinv = L.buf<T>().dinvD;
+      a.dout = x;
+    } else {
+      a.x = x;
+    }
     a.w = L.buf<T>().wD;
     a.excl = l == 0 ? s.act : L.exclD;
     a.b = b;
@@ -406,7 +423,8 @@ void residual_op(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const 
 
 template <class T>
 void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T* x, const T* d,
-               T* xo, T* dout, double cd, double cr, const T* xc = nullptr, int dot_slot = -1) {
+               T* xo, T* dout, double cd, double cr, const T* xc = nullptr, int dot_slot = -1,
+               double x0 = 0.0) {
   Level& L = s.lv[l];
   const bool dot = dot_slot >= 0;
   if (phys == ELASTIC) {
@@ -416,6 +434,8 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
       a.gc = s.lv[l + 1].g;
     }
     a.x = x;
+    a.x0b = x0 > 0.0;
+    a.c0 = T(x0);
     a.alpha = alpha_of<T>(s);
     a.coef = L.buf<T>().coefE;
     a.b = b;
@@ -435,6 +455,8 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
       a.gc = s.lv[l + 1].g;
     }
     a.x = x;
+    a.x0b = x0 > 0.0;
+    a.c0 = T(x0);
     a.w = L.buf<T>().wD;
     a.excl = l == 0 ? s.act : L.exclD;
     a.b = b;
@@ -450,6 +472,25 @@ void cheb_step(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, const T*
   }
 }
 
+// Coefficients of the first `steps` Chebyshev steps on D_l1^{-1} A over [lmin, lmax] = [0.1, 1]
+// (l1 scaling bounds the spectrum by 1): d_k = cd[k] d_{k-1} + cr[k] D^-1 (b - A x_{k-1}).
+static void cheb_coefs(int steps, double* cd, double* cr) {
+  const double lmax = 1.0, lmin = 0.1;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < steps; ++k) {
+    if (k == 0) {
+      cd[k] = 0.0;
+      cr[k] = 1.0 / theta;
+    } else {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      cd[k] = rn * rho;
+      cr[k] = 2.0 * rn / delta;
+      rho = rn;
+    }
+  }
+}
+
 // Chebyshev smoothing on D_l1^{-1} A over [lmin, lmax] = [0.1, 1] (l1 scaling bounds the
 // spectrum by 1).  Starts from x (x0 == nullptr: from zero); result written to x.
 // xc (optional, not with from_zero): the coarse-grid correction, prolongated into x by the first
@@ -461,27 +502,19 @@ void smooth(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, bool 
   LevelBuf<T>& B = s.lv[l].buf<T>();
   const int nc = phys == ELASTIC ? 2 : 1;
   const size_t nd = (size_t)nc * s.lv[l].g.n;
-  const double lmax = 1.0, lmin = 0.1;
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-  double rho = 1.0 / sigma;
-  // From zero the first step reads no x (the kernel takes x = 0), so no fill is needed, and the
-  // first output buffer is chosen so that the last step writes into x.
+  double cdk[8 * MAX_CHEB], crk[8 * MAX_CHEB];  // up to the 8 * degree steps of a coarsest level
+  cheb_coefs(steps, cdk, crk);
+  // From zero the first step is pointwise, x = d = c0 D^-1 b: alone it is a launch that reads no
+  // x (no fill needed); followed by more steps, the second forms it from b and dinv as it stages
+  // its nodes, so it takes no launch of its own.  The first output buffer is chosen so that the
+  // last step writes into x.
+  const int k0 = from_zero && steps >= 2 ? 1 : 0;
   T* other = B.xt;
   T *cx = from_zero ? nullptr : x, *cd_ = nullptr, *nd_ = B.d;
-  T* nx_ = from_zero ? ((steps & 1) ? x : other) : other;
-  for (int k = 0; k < steps; ++k) {
-    double cdk, crk;
-    if (k == 0) {
-      cdk = 0.0;
-      crk = 1.0 / theta;
-    } else {
-      double rn = 1.0 / (2.0 * sigma - rho);
-      cdk = rn * rho;
-      crk = 2.0 * rn / delta;
-      rho = rn;
-    }
-    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk, crk, k == 0 ? xc : nullptr,
-                 k == steps - 1 ? dot_slot : -1);
+  T* nx_ = from_zero ? (((steps - k0) & 1) ? x : other) : other;
+  for (int k = k0; k < steps; ++k) {
+    cheb_step<T>(s, st, phys, l, b, cx, cd_, nx_, nd_, cdk[k], crk[k], k == 0 ? xc : nullptr,
+                 k == steps - 1 ? dot_slot : -1, k0 == 1 && k == 1 ? crk[0] : 0.0);
     // rotate buffers: new x becomes current; the old current x buffer is free for the next step
     T* ox = cx;
     cx = nx_;
@@ -528,7 +561,8 @@ int tail_first(pf_sim& s, int phys) {
   return best;
 }
 
-void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x, int deg) {
+void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x, int deg,
+                 const float* rf) {
   const int nlev = (int)s.lv.size(), l0 = s.tail_first[phys];
   const int nc = phys == ELASTIC ? 2 : 1;
   TailArgs a{};
@@ -536,12 +570,20 @@ void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x,
   a.deg = s.cdeg;
   a.deg0 = l0 == 0 ? deg : s.cdeg;
   a.first_level = l0;
-  a.dense = 1;
-  a.coarse_steps = 8 * s.cdeg;
+  double cdk[MAX_CHEB], crk[MAX_CHEB];
+  cheb_coefs(MAX_CHEB, cdk, crk);
+  for (int k = 0; k < MAX_CHEB; ++k) {
+    a.cheb_cd[k] = float(cdk[k]);
+    a.cheb_cr[k] = float(crk[k]);
+  }
   const Level& Lc = s.lv[nlev - 1];
   a.Ainv = phys == ELASTIC ? Lc.f32.AEi : Lc.f32.ADi;
   a.b_in = b;
   a.x_out = x;
+  if (rf) {  // right-hand side restricted from the finer level's residual by the kernel
+    a.rf = rf;
+    a.gf = s.lv[l0 - 1].g;
+  }
   int off = 0;
   for (int k = 0; k < a.nl; ++k) {
     const Level& L = s.lv[l0 + k];
@@ -562,25 +604,38 @@ void launch_tail(pf_sim& s, cudaStream_t st, int phys, const float* b, float* x,
     off += (int)tail_level_floats(L.g, nc);
   }
   a.orec = off;  // records of the largest level (the first)
-  off += (phys == ELASTIC ? 3 : 4) * s.lv[l0].g.nelem;
+  const int nrec = (phys == ELASTIC ? 3 : 4) * s.lv[l0].g.nelem;
+  const int nd = nc * s.lv[nlev - 1].g.n, np = (nd + 1) / 2;
+  a.dense_slices = std::max(1, std::min(TAIL_THREADS / np, nrec / nd));
+  off += std::max(nrec, a.dense_slices * nd);
   tail_vcycle(st, nc, a, (size_t)off * sizeof(float));
 }
 
 // Returns true if dot_slot received b . x from the last level-0 smoothing step (false when the
 // single-block tail ran this level or no slot was asked for).
+// rf (levels below the finest): b is not formed yet; it is the restriction P^T rf of the finer
+// level's residual.  The single-block tail forms it as it loads the level; otherwise it is
+// formed into b (this level's right-hand side buffer) by the restriction kernel first.
 template <class T>
 bool vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int deg,
-            int dot_slot = -1) {
+            int dot_slot = -1, const T* rf = nullptr) {
+  const int nc = phys == ELASTIC ? 2 : 1;
   if constexpr (std::is_same<T, float>::value) {
     if (l == tail_first(s, phys)) {
-      launch_tail(s, st, phys, b, x, deg);
+      launch_tail(s, st, phys, b, x, deg, rf);
       return false;
     }
   }
   Level& L = s.lv[l];
   LevelBuf<T>& B = L.buf<T>();
-  const int nc = phys == ELASTIC ? 2 : 1;
   const int nlev = s.nl_active;  // levels in use (mg_levels_max)
+  const int dl = l == 0 ? deg : s.cdeg;  // smoothing steps on this level
+  if (rf) {
+    const Level& F = s.lv[l - 1];
+    restrict_res<T>(st, F.g, L.g, nc, phys == ELASTIC ? 0 : 2, rf, const_cast<T*>(b),
+                    phys == DAMAGE ? L.exclD : nullptr, l - 1);
+    rf = nullptr;
+  }
   if (l == nlev - 1) {
     if (L.dense && nlev > 1) {
       coarse_solve<T>(st, nc * L.g.n, phys == ELASTIC ? B.AEi : B.ADi, b, x);
@@ -591,12 +646,15 @@ bool vcycle(pf_sim& s, cudaStream_t st, int phys, int l, const T* b, T* x, int d
   }
   Level& C = s.lv[l + 1];
   LevelBuf<T>& BC = C.buf<T>();
-  const int dl = l == 0 ? deg : s.cdeg;  // smoothing steps on this level
-  smooth<T>(s, st, phys, l, b, x, true, dl);
-  residual_op<T>(s, st, phys, l, b, x, B.r);
-  restrict_res<T>(st, L.g, C.g, nc, phys == ELASTIC ? 0 : 2, B.r, BC.b,
-                  phys == DAMAGE ? C.exclD : nullptr, l);
-  vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg);
+  if (dl == 1) {  // the one pre-smoothing step from zero is pointwise: formed by the residual
+    double c0, r0;
+    cheb_coefs(1, &c0, &r0);
+    residual_op<T>(s, st, phys, l, b, x, B.r, r0);
+  } else {
+    smooth<T>(s, st, phys, l, b, x, true, dl);
+    residual_op<T>(s, st, phys, l, b, x, B.r);
+  }
+  vcycle<T>(s, st, phys, l + 1, BC.b, BC.x, deg, -1, B.r);
   // prolongation x += P x_c fused into the first post-smoothing step
   smooth<T>(s, st, phys, l, b, x, false, dl, BC.x, dot_slot);
   return dot_slot >= 0;
@@ -1914,6 +1972,8 @@ static pf_status check_opts(const pf_solver_opts* o) {
   if (!(o->omega > 0.0 && o->omega < 2.0)) return fail(PF_EINVAL, "omega must lie in (0, 2)");
   if (o->am_maxit < 1 || o->cg_maxit < 1 || o->rs_maxit < 1 || o->mg_degree < 1)
     return fail(PF_EINVAL, "iteration limits must be positive");
+  if (o->mg_degree > MAX_CHEB || o->mg_coarse_degree > MAX_CHEB)
+    return fail(PF_EINVAL, "Chebyshev degrees must not exceed 16");
   if (!(o->am_forcing >= 0.0) || !(o->am_forcing_max >= 0.0))
     return fail(PF_EINVAL, "am_forcing and am_forcing_max must be >= 0");
   if (o->omega_rule != 0 && o->omega_rule != 1) return fail(PF_EINVAL, "omega_rule must be 0 or 1");

@@ -215,8 +215,11 @@ struct ElasticArgs {
   const T* xc;        // M_CHEB: if set, x is read as x + P xc (prolongation from grid gc fused
   Grid gc;            // into the first post-smoothing step)
   T cd, cr;           // M_CHEB coefficients
+  int x0b;            // M_CHEB, M_RESB: x is the first Chebyshev step from zero, c0 D^-1 b (0 on
+  T c0;               // prescribed dofs), formed from b and dinv as it is read; M_CHEB takes it
+                      // as the previous update too, M_RESB writes it to dout
   T* y;               // output (2n); M_CHEB: new x
-  T* dout;            // M_CHEB: new d
+  T* dout;            // M_CHEB: new d; M_RESB with x0b: the first step's x
   RedSlot slot;
   int coarse;         // launch accounting: multigrid level (0 = finest)
   int df;             // M_RESID with T = double: 1 computes in double-float (the mixed path)
@@ -346,6 +349,13 @@ struct ElasticOp {
       v.ux = to_c<C>(u.x);
       v.uy = to_c<C>(u.y);
     }
+    if constexpr (MODE == M_CHEB || MODE == M_RESB) {
+      if (args.x0b) {  // the step from zero, rounded as the M_CHEB store rounds it
+        const Pair<T> b = ld_pair(args.b, node), di = ld_pair(args.dinv, node);
+        v.ux = args.c0 * di.x * b.x;
+        v.uy = args.c0 * di.y * b.y;
+      }
+    }
     if constexpr (MODE == M_CHEB) {
       if (args.xc) {
         v.ux += to_c<C>(prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0));
@@ -433,10 +443,12 @@ struct ElasticOp {
         const Pair<T> b = ld_pair(args.b, node);
         T rx = f0 ? T(0) : b.x - fx, ry = f1 ? T(0) : b.y - fy;
         st_pair(args.y, node, rx, ry);
+        if (args.x0b) st_pair(args.dout, node, own.ux, own.uy);
         if (DOT) red[0] += rx * rx + ry * ry;
       } else if (MODE == M_CHEB) {
         const Pair<T> b = ld_pair(args.b, node), di = ld_pair(args.dinv, node);
-        const Pair<T> p = args.d ? ld_pair(args.d, node) : Pair<T>{T(0), T(0)};
+        const Pair<T> p = args.d ? ld_pair(args.d, node)
+                                 : (args.x0b ? Pair<T>{own.ux, own.uy} : Pair<T>{T(0), T(0)});
         T rx = b.x - fx, ry = b.y - fy;
         T dx = f0 ? T(0) : args.cd * p.x + args.cr * di.x * rx;
         T dy = f1 ? T(0) : args.cd * p.y + args.cr * di.y * ry;
@@ -465,9 +477,11 @@ struct DamageArgs {
   Grid gc;
   const double* lo;     // M_GRAD/M_TRIAL: lower bound alpha_prev
   T cd, cr;             // M_CHEB coefficients; M_TRIAL: cd = step mu
+  int x0b;              // M_CHEB, M_RESB: x is the first Chebyshev step from zero, c0 D^-1 b (0 on
+  T c0;                 // excluded nodes), as in ElasticArgs
   double zeta;
   T* y;                 // output: M_APPLY..M_CHEB result; M_GRAD/M_TRIAL: F
-  T* dout;              // M_CHEB new d; M_GRAD/M_TRIAL: Phi
+  T* dout;              // M_CHEB new d; M_GRAD/M_TRIAL: Phi; M_RESB with x0b: the first step's x
   T* rhs;               // M_GRAD/M_TRIAL: -F on the inactive set, 0 elsewhere
   T* xt;                // M_TRIAL: trial point
   uint8_t* act;         // M_GRAD/M_TRIAL: active flags written
@@ -532,6 +546,9 @@ struct DamageOp {
       v.p = to_c<C>(T(trial_value(node, X2, Y2)));
     } else {
       v.p = args.x ? to_c<C>(args.x[node]) : C(0);  // M_CHEB without x: smoothing from zero
+      if constexpr (MODE == M_CHEB || MODE == M_RESB) {
+        if (args.x0b) v.p = args.c0 * args.dinv[node] * args.b[node];  // the step from zero
+      }
       if constexpr (MODE == M_CHEB) {
         if (args.xc) v.p += to_c<C>(prolong_value(g, args.gc, 1, args.xc, node, X2, Y2, 0));
       }
@@ -625,9 +642,10 @@ struct DamageOp {
       } else if (MODE == M_RESB) {
         T r = (args.excl && args.excl[node]) ? T(0) : args.b[node] - f;
         args.y[node] = r;
+        if (args.x0b) args.dout[node] = own.p;
         if (DOT) red[0] += r * r;
       } else if (MODE == M_CHEB) {
-        T dp = args.d ? args.d[node] : T(0);
+        T dp = args.d ? args.d[node] : (args.x0b ? own.p : T(0));
         const T bn = args.b[node];
         T dn = (args.excl && args.excl[node]) ? T(0) : args.cd * dp + args.cr * args.dinv[node] * (bn - f);
         args.dout[node] = dn;

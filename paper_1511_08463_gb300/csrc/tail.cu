@@ -152,30 +152,27 @@ __device__ void apply_level(const TailLevel& L, const float* coef, const float* 
   __syncthreads();
 }
 
-// `steps` Chebyshev steps on D_l1^{-1} A over [0.1, 1] (the grid-wide smoother's recurrence and
-// update); the new iterate goes to xn and the buffers are swapped, as the grid-wide path rotates them.
+// `steps` Chebyshev steps on D_l1^{-1} A over [0.1, 1] with the grid-wide smoother's recurrence
+// coefficients (computed once on the host) and update; the new iterate goes to xn and the
+// buffers are swapped, as the grid-wide path rotates them.
 template <int KIND, int NC>
-__device__ void smooth(const TailLevel& L, TailBufs& B, float* rec, bool from_zero, int steps) {
+__device__ void smooth(const TailArgs& a, const TailLevel& L, TailBufs& B, float* rec,
+                       bool from_zero, int steps) {
   const int nd = NC * L.g.n;
-  if (from_zero) {
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) B.x[i] = 0.f;
-    __syncthreads();
-  }
-  const double lmax = 1.0, lmin = 0.1;
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-  double rho = 1.0 / sigma;
-  for (int k = 0; k < steps; ++k) {
-    double cdk, crk;
-    if (k == 0) {
-      cdk = 0.0;
-      crk = 1.0 / theta;
-    } else {
-      const double rn = 1.0 / (2.0 * sigma - rho);
-      cdk = rn * rho;
-      crk = 2.0 * rn / delta;
-      rho = rn;
+  int k0 = 0;
+  if (from_zero && steps > 0) {  // the first step from zero is pointwise: x = d = c0 D^-1 b
+    const float c0 = a.cheb_cr[0];
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+      const int node = i / NC, c = i - node * NC;
+      const float v = (B.fz[node] >> c) & 1 ? 0.f : c0 * B.dinv[i] * B.b[i];
+      B.d[i] = v;
+      B.x[i] = v;
     }
-    const float cd = float(cdk), cr = float(crk);
+    __syncthreads();
+    k0 = 1;
+  }
+  for (int k = k0; k < steps; ++k) {
+    const float cd = a.cheb_cd[k], cr = a.cheb_cr[k];
     const bool first = k == 0;
     apply_level<KIND, NC>(L, B.coef, B.x, rec, [&](int node, const float* f) {
 #pragma unroll
@@ -220,12 +217,17 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailArgs a) {
       B[l].fz[node] = f;
     }
   }
-  for (int i = tid; i < NC * a.L[0].g.n; i += nt) B[0].b[i] = a.b_in[i];
+  if (a.rf) {
+    for (int node = tid; node < a.L[0].g.n; node += nt)
+      restrict_node(a.gf, a.L[0].g, NC, NC == 2 ? 0 : 2, a.rf, B[0].b, a.L[0].excl, node);
+  } else {
+    for (int i = tid; i < NC * a.L[0].g.n; i += nt) B[0].b[i] = a.b_in[i];
+  }
   __syncthreads();
   const int comp_base = NC == 2 ? 0 : 2;
   for (int l = 0; l + 1 < a.nl; ++l) {  // down: pre-smooth, residual, restrict
     const TailLevel& L = a.L[l];
-    smooth<KIND, NC>(L, B[l], rec, true, l == 0 ? a.deg0 : a.deg);
+    smooth<KIND, NC>(a, L, B[l], rec, true, l == 0 ? a.deg0 : a.deg);
     TailBufs& Bl = B[l];
     apply_level<KIND, NC>(L, Bl.coef, Bl.x, rec, [&](int node, const float* f) {
 #pragma unroll
@@ -240,16 +242,39 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailArgs a) {
     __syncthreads();
   }
   const int lc = a.nl - 1;  // coarsest level of the tail
-  if (a.dense) {
-    const int n = NC * a.L[lc].g.n;
+  {  // dense coarsest solve x = Ainv b with the stored inverse: each thread takes a pair of
+     // outputs over one of dense_slices column ranges (many independent loads in flight across
+     // the block instead of one long chain per output), then the slices are summed in order
+    const int n = NC * a.L[lc].g.n, np = (n + 1) >> 1, S = a.dense_slices;
+    const float* bc = B[lc].b;
+    for (int t = tid; t < np * S; t += nt) {
+      const int ip = t % np, sl = t / np, i = 2 * ip;
+      const int j0 = sl * n / S, j1 = (sl + 1) * n / S;
+      float s0 = 0.f, s1 = 0.f;
+      if ((n & 1) == 0) {  // rows of even length: (i, i+1) is one aligned 8-byte load
+#pragma unroll 8
+        for (int j = j0; j < j1; ++j) {
+          const float2 v = *reinterpret_cast<const float2*>(a.Ainv + (size_t)j * n + i);
+          s0 += v.x * bc[j];
+          s1 += v.y * bc[j];
+        }
+      } else {
+#pragma unroll 8
+        for (int j = j0; j < j1; ++j) {
+          s0 += a.Ainv[(size_t)j * n + i] * bc[j];
+          if (i + 1 < n) s1 += a.Ainv[(size_t)j * n + i + 1] * bc[j];
+        }
+      }
+      rec[sl * n + i] = s0;
+      if (i + 1 < n) rec[sl * n + i + 1] = s1;
+    }
+    __syncthreads();
     for (int i = tid; i < n; i += nt) {
-      float acc = 0.f;
-      for (int j = 0; j < n; ++j) acc += a.Ainv[(size_t)j * n + i] * B[lc].b[j];
+      float acc = rec[i];
+      for (int sl = 1; sl < S; ++sl) acc += rec[sl * n + i];
       B[lc].x[i] = acc;
     }
     __syncthreads();
-  } else {
-    smooth<KIND, NC>(a.L[lc], B[lc], rec, true, a.coarse_steps);
   }
   for (int l = a.nl - 2; l >= 0; --l) {  // up: prolong, post-smooth
     const TailLevel& L = a.L[l];
@@ -257,7 +282,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailArgs a) {
     for (int node = tid; node < L.g.n; node += nt)
       prolong_node(L.g, C.g, NC, comp_base, B[l + 1].x, B[l].x, B[l].excl, node);
     __syncthreads();
-    smooth<KIND, NC>(L, B[l], rec, false, l == 0 ? a.deg0 : a.deg);
+    smooth<KIND, NC>(a, L, B[l], rec, false, l == 0 ? a.deg0 : a.deg);
   }
   for (int i = tid; i < NC * a.L[0].g.n; i += nt) a.x_out[i] = B[0].x[i];
 }

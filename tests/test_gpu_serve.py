@@ -115,7 +115,9 @@ def test_solve_batch_concurrent_equals_sequential():
 
 def test_served_jobs_match_oracle():
     """Jobs that ran through the serving loop, next to each other, against the oracle's
-    Algorithm 2 on the same schedules: energies at every load step, fields at the end."""
+    Algorithm 2 on the same schedules: energies at every load step; fields at the end where the
+    path is stable (the notched square; where the bar's crack nucleates is a bifurcation decided
+    by rounding, so only its energies are compared)."""
     need_gpu()
     from oracle import am
     from oracle.problem import Problem
@@ -134,7 +136,10 @@ def test_served_jobs_match_oracle():
         for (t, dT), rep in zip(w.loads, r["reports"]):
             o = am.load_step(p, t, dT, omega=w.omega, tol=1e-10, maxit=5000)
             assert o["status"] == "converged"
-            np.testing.assert_allclose(rep["energy"], o["energy"], rtol=1e-8, atol=1e-14)
-        assert rel_max(r["u"], p.u) <= 1e-6
-        assert np.abs(r["alpha"] - p.alpha).max() <= 1e-6
+            # absolute floor: at the bar's critical load the damage is zero up to rounding
+            np.testing.assert_allclose(rep["energy"], o["energy"], rtol=1e-8,
+                                       atol=1e-10 * abs(o["energy"][2]))
+        if w.name.startswith("notched"):
+            assert rel_max(r["u"], p.u) <= 1e-6
+            assert np.abs(r["alpha"] - p.alpha).max() <= 1e-6
     assert res[0]["alpha"].max() > 0.5  # the notched job grew a crack
