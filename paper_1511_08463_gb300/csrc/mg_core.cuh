@@ -135,6 +135,27 @@ __device__ __forceinline__ T prolong_value(const Grid& gf, const Grid& gc, int n
   return T(0.5) * (cget(gc, xc, false, I + pi, J + pj, c, ncomp) + cget(gc, xc, true, I, J, c, ncomp));
 }
 
+// The same interpolation as prolong_value, as the mean of two coarse nodes (a == b at a fine node
+// that coincides with a coarse one): (P x_c)(node) = (x_c[a] + x_c[b]) / 2, with no branch on
+// the node's parity, so that all components can be read with one access per coarse node.
+__device__ __forceinline__ void prolong_nodes(const Grid& gf, const Grid& gc, int node, int X2,
+                                              int Y2, int& a, int& b) {
+  if (node < gf.nv) {
+    const int i = X2 / 2, j = Y2 / 2, I = i >> 1, J = j >> 1, pi = i & 1, pj = j & 1;
+    if (gf.kind == CROSSED && pi && pj) {  // fine vertex at a coarse cell centre
+      a = b = gc.nv + J * gc.nx + I;
+    } else {
+      a = J * (gc.nx + 1) + I;
+      b = (J + pj) * (gc.nx + 1) + I + pi;
+    }
+  } else {
+    const int cc = node - gf.nv, j = cc / gf.nx, i = cc - j * gf.nx;
+    const int I = i >> 1, J = j >> 1;
+    a = (J + (j & 1)) * (gc.nx + 1) + I + (i & 1);
+    b = gc.nv + J * gc.nx + I;
+  }
+}
+
 // x_f(node) += (P x_c)(node) (P1 interpolation), except on prescribed and excluded fine dofs.
 template <class T>
 __device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, int ncomp,

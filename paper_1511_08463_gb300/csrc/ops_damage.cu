@@ -52,8 +52,9 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const DamageArgs<T>&
       return;
     }
   }
-  const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED : M == M_RESB ? KC_DM_RESB
-                 : M == M_CHEB ? KC_DM_CHEB : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;
+  const int base = M == M_APPLY ? KC_DM_APPLY : M == M_MASKED ? KC_DM_MASKED
+                 : M == M_RESB ? (a.x0b ? KC_DM_RESB_Z : KC_DM_RESB)
+                 : M == M_CHEB ? (a.x0b ? KC_DM_CHEB_Z : KC_DM_CHEB) : M == M_GRAD ? KC_DM_GRAD : KC_DM_TRIAL;
   DamageOp<T, K, M, D> op;
   op.g = g;
   op.m = m;

@@ -50,8 +50,9 @@ static void go(cudaStream_t s, const Grid& g, const Mat& m, const ElasticArgs<T>
       return;
     }
   }
-  const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED : M == M_RESB ? KC_EL_RESB
-                 : M == M_RESID ? KC_EL_RESID : KC_EL_CHEB;
+  const int base = M == M_APPLY ? KC_EL_APPLY : M == M_MASKED ? KC_EL_MASKED
+                 : M == M_RESB ? (a.x0b ? KC_EL_RESB_Z : KC_EL_RESB)
+                 : M == M_RESID ? KC_EL_RESID : (a.x0b ? KC_EL_CHEB_Z : KC_EL_CHEB);
   ElasticOp<T, K, C, M, E, D> op;
   op.g = g;
   op.m = m;

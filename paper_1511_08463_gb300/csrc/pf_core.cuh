@@ -189,11 +189,20 @@ __device__ __forceinline__ void block_reduce_finalize(VT (&v)[NV], RedSlot slot)
   if (last) {
     __threadfence();
     unsigned nb = gridDim.x * gridDim.y;
-    // each thread sums a strided subset in fixed order, then a fixed-order tree
+    // each thread sums a strided subset in fixed order, then a fixed-order tree; the partials
+    // are read from L2 eight at a time (all in flight together) and added in the same order
     for (int q = 0; q < NV; ++q) {
       double x = MAX ? -INFINITY : 0.0;
-      for (unsigned b = tid; b < nb; b += nthreads) {
-        double y = ((volatile double*)slot.part)[b * NV + q];
+      unsigned b = tid;
+      for (; b + 7u * nthreads < nb; b += 8u * nthreads) {
+        double y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) y[u] = __ldcg(slot.part + (size_t)(b + u * nthreads) * NV + q);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x = MAX ? fmax(x, y[u]) : x + y[u];
+      }
+      for (; b < nb; b += nthreads) {
+        const double y = __ldcg(slot.part + (size_t)b * NV + q);
         x = MAX ? fmax(x, y) : x + y;
       }
       for (int o = 16; o > 0; o >>= 1) {

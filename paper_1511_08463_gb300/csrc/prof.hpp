@@ -18,6 +18,9 @@ enum KernelClass : int {
   KC_DM_APPLY, KC_DM_MASKED, KC_DM_RESB, KC_DM_CHEB, KC_DM_GRAD, KC_DM_TRIAL,
   KC_VECTOR, KC_REDUCE, KC_TRANSFER, KC_SETUP, KC_COARSE, KC_TAIL,
   KC_EL_RESID_DF, KC_DM_GRAD_DF, KC_DM_TRIAL_DF,  // FP64 in/out, double-float arithmetic
+  // smoothing from zero: the first (pointwise) Chebyshev step formed inside the second one's
+  // launch, or inside the residual's when it is the only pre-smoothing step
+  KC_EL_CHEB_Z, KC_DM_CHEB_Z, KC_EL_RESB_Z, KC_DM_RESB_Z,
   KC_BASE_COUNT
 };
 // class id = base + KC_BASE_COUNT * (precision * KC_LEVELS + multigrid level), so that one class

@@ -358,8 +358,11 @@ struct ElasticOp {
     }
     if constexpr (MODE == M_CHEB) {
       if (args.xc) {
-        v.ux += to_c<C>(prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 0));
-        v.uy += to_c<C>(prolong_value(g, args.gc, 2, args.xc, node, X2, Y2, 1));
+        int ca, cb;
+        prolong_nodes(g, args.gc, node, X2, Y2, ca, cb);
+        const Pair<T> pa = ld_pair(args.xc, ca), pb = ld_pair(args.xc, cb);
+        v.ux += to_c<C>(T(0.5) * (pa.x + pb.x));
+        v.uy += to_c<C>(T(0.5) * (pa.y + pb.y));
       }
     }
     if (MODE != M_APPLY && MODE != M_RESID) {
@@ -550,7 +553,11 @@ struct DamageOp {
         if (args.x0b) v.p = args.c0 * args.dinv[node] * args.b[node];  // the step from zero
       }
       if constexpr (MODE == M_CHEB) {
-        if (args.xc) v.p += to_c<C>(prolong_value(g, args.gc, 1, args.xc, node, X2, Y2, 0));
+        if (args.xc) {
+          int ca, cb;
+          prolong_nodes(g, args.gc, node, X2, Y2, ca, cb);
+          v.p += to_c<C>(T(0.5) * (args.xc[ca] + args.xc[cb]));
+        }
       }
       if ((MODE == M_MASKED || MODE == M_RESB || MODE == M_CHEB) && args.excl && args.excl[node]) v.p = C(0);
     }
