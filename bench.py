@@ -578,6 +578,31 @@ def run_ours(args):
     dominant = max(prof_tab.items(), key=lambda kv: kv[1]["ms"])[0] if prof_tab else None
     sim.set_fields(*snap)
     torch.cuda.synchronize()
+    # the FP64-data kernels: the same load step replayed on the FP64 path, per-launch times of
+    # its FP64 kernels against the mixed path's double-float ones
+    df_vs_fp64 = None
+    if args.precision == "mixed" and world == 1:
+        lib.pf_prof_reset()
+        lib.pf_prof_enable(1, -1)
+        sim.load_step(*w.loads[W0], S.make_opts(algo=args.algo, omega=w.omega, precision="fp64",
+                                               use_graphs=0, am_maxit=AM_MAXIT),
+                      allow_notconv=True)
+        torch.cuda.synchronize()
+        lib.pf_prof_enable(0, -1)
+        tab64 = B.prof_table()
+        sim.set_fields(*snap)
+        torch.cuda.synchronize()
+        pairs = [("elastic_resid_df_f64_l0", "elastic_resid_f64_l0"),
+                 ("damage_grad_df_f64_l0", "damage_grad_f64_l0"),
+                 ("damage_trial_df_f64_l0", "damage_trial_f64_l0"),
+                 ("damage_q_df_f64_l0", "damage_q_f64_l0")]
+        df_vs_fp64 = {}
+        for a, b in pairs:
+            if a in prof_tab and b in tab64 and prof_tab[a]["timed"] and tab64[b]["timed"]:
+                ua = prof_tab[a]["ms"] * 1e3 / prof_tab[a]["timed"]
+                ub = tab64[b]["ms"] * 1e3 / tab64[b]["timed"]
+                df_vs_fp64[a] = {"df_us_per_launch": round(ua, 1), "fp64_kernel": b,
+                                 "fp64_us_per_launch": round(ub, 1), "speedup": round(ub / ua, 2)}
 
     # ---- main pass over the schedule (CUDA graphs on) -------------------------------------------
     # Every step from W0+1 on runs in order, so each step starts from the state its predecessor
@@ -780,7 +805,9 @@ def run_ours(args):
             "kernel_classes_replay_step": {k: {"ms": round(v["ms"], 3),
                                                "launches": v["launches"]}
                                            for k, v in sorted(prof_tab.items(),
-                                                              key=lambda kv: -kv[1]["ms"])[:14]},
+                                                              key=lambda kv: -kv[1]["ms"])
+                                           if v["ms"] >= 1.0 or "_df" in k},
+            "df_kernels_vs_fp64": df_vs_fp64,
             "replay_step_seconds_no_graphs": replay_s,
         }
         print(json.dumps(line), flush=True)

@@ -4,14 +4,20 @@
 // Dekker's TwoProduct for products.  Each result is within a few units of 2^-48 of the exact one,
 // relative to the operands' magnitudes, so sums and products of FP64 inputs keep ~14 significant
 // digits while running on the FP32 units (FP64 arithmetic throughput is a small fraction of FP32
-// on this GPU).  Conversions from and to double cost one FP64 subtraction or addition.
+// on this GPU).  A double is split into hi + lo with integer operations on its bit pattern (no
+// FP64 instruction); the conversion back costs one FP64 addition.
 //
 // The file must be compiled without floating-point reassociation (nvcc's default); products use
 // explicit fmaf, and no expression here has a product that contraction could fuse.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
 
 namespace pf {
+
+struct dfloat;
+__host__ __device__ inline dfloat df_from_double(double d);
 
 struct dfloat {
   float hi, lo;
@@ -19,9 +25,59 @@ struct dfloat {
   __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
   // exact for the small integers of the gradient tables
   __host__ __device__ explicit constexpr dfloat(int i) : hi(float(i)), lo(0.f) {}
-  __host__ __device__ explicit dfloat(double d) : hi(float(d)), lo(float(d - double(float(d)))) {}
+  __host__ __device__ explicit dfloat(double d);
   __host__ __device__ explicit operator double() const { return double(hi) + double(lo); }
 };
+
+__host__ __device__ inline uint64_t df_bits(double d) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(d);
+#else
+  uint64_t b;
+  memcpy(&b, &d, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ inline float df_float_of_bits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+
+// hi = d rounded to FP32 (to nearest, ties away from zero), lo = the rest rounded to FP32, both
+// from the IEEE-754 fields of d: sign s, biased exponent E, 52-bit fraction F.  hi keeps the top
+// 23 fraction bits (+1 in the last place when the 29 bits below are at least half of it); the
+// remainder r, |r| <= 2^28, is worth r 2^(E-1075).  Normal doubles with 2^-126 <= |d| < 2^127
+// take this path (lo is flushed to zero below 2^-74, an absolute error under 2^-98); zeros give
+// (0, 0); anything else (subnormals, huge values, infinities, NaN) goes through FP64 conversions.
+__host__ __device__ inline dfloat df_from_double(double d) {
+  const uint64_t b = df_bits(d);
+  const int E = int((b >> 52) & 0x7FF);
+  if (E >= 897 && E <= 1149) {
+    const uint32_t sign = uint32_t(b >> 32) & 0x80000000u;
+    uint32_t hb = sign | (uint32_t(E - 896) << 23) | uint32_t((b >> 29) & 0x7FFFFFu);
+    int32_t r = int32_t(b & 0x1FFFFFFFu);
+    if (r >= (1 << 28)) {  // round hi up (a carry into the exponent is the right result)
+      hb += 1u;
+      r -= 1 << 29;
+    }
+    float lo = 0.f;
+    if (E >= 949 && r != 0) {
+      const float scale = df_float_of_bits(uint32_t(E - 948) << 23);  // 2^(E - 1075)
+      lo = float(r) * scale;
+      if (sign) lo = -lo;
+    }
+    return dfloat(df_float_of_bits(hb), lo);
+  }
+  if ((b << 1) == 0) return dfloat(0.f, 0.f);
+  const float h = float(d);
+  return dfloat(h, float(d - double(h)));
+}
+__host__ __device__ inline dfloat::dfloat(double d) : dfloat(df_from_double(d)) {}
 
 __device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
   s = a + b;

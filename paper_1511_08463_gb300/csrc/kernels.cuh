@@ -69,7 +69,7 @@ template <class T>
 void elastic_coef(cudaStream_t s, const Grid& g, const Mat& m, const T* alpha, T* coef);
 // q_T = A0 eps_eff : eps_eff (FP64); w64 = q + c2, w32 = float(q + c2)
 void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
-              double* q, double* w64, float* w32);
+              double* q, double* w64, float* w32, bool df = false);  // df: double-float arithmetic
 // energies: out[0] elastic, out[1] surface
 void energy(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* alpha,
             const double* eig, RedSlot slot);

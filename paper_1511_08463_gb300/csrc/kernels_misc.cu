@@ -416,9 +416,78 @@ __global__ void k_damage_q(Grid g, Mat m, const double* u, const double* eig, do
     if (w32) w32[cell * NE + t] = (float)(qq + m.c2);
   }
 }
+// The same energy densities in double-float arithmetic on the FP64 data (the mixed path): strains
+// from the gradient tables (exact additions for their +-1 weights), then q = (lambda + 2 mu)
+// (exx^2 + eyy^2) + 2 lambda exx eyy + mu gxy^2, written as FP64.
+template <int KIND, int t>
+__device__ __forceinline__ void q_elem_df(const Consts<dfloat>& cs, dfloat lam2, dfloat c2,
+                                          const dfloat (&ux)[3], const dfloat (&uy)[3], dfloat e0,
+                                          bool eigen, double* q, double* w64, float* w32, int e) {
+  constexpr int a0 = gx(KIND, t, 0), a1 = gx(KIND, t, 1), a2 = gx(KIND, t, 2);
+  constexpr int b0 = gy(KIND, t, 0), b1 = gy(KIND, t, 1), b2 = gy(KIND, t, 2);
+  dfloat exx = cs.ihx * gsum<a0, a1, a2>(ux[0], ux[1], ux[2]);
+  dfloat eyy = cs.ihy * gsum<b0, b1, b2>(uy[0], uy[1], uy[2]);
+  const dfloat gxy = cs.ihy * gsum<b0, b1, b2>(ux[0], ux[1], ux[2]) +
+                     cs.ihx * gsum<a0, a1, a2>(uy[0], uy[1], uy[2]);
+  if (eigen) {
+    exx -= e0;
+    eyy -= e0;
+  }
+  const dfloat qq = cs.lam2mu * (exx * exx + eyy * eyy) + lam2 * (exx * eyy) + cs.mu * (gxy * gxy);
+  q[e] = double(qq);
+  if (w64 || w32) {
+    const double w = double(qq + c2);
+    if (w64) w64[e] = w;
+    if (w32) w32[e] = (float)w;
+  }
+}
+template <int KIND>
+__global__ void k_damage_q_df(Grid g, Consts<dfloat> cs, dfloat lam2, dfloat c2, const double* u,
+                              const double* eig, double* q, double* w64, float* w32) {
+  pdl_enter();
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncell) return;
+  constexpr int NE = elems_per_cell(KIND);
+  const int cj = cell / g.nx, ci = cell - cj * g.nx;
+  const int v00 = cj * (g.nx + 1) + ci, v10 = v00 + 1, v01 = v00 + g.nx + 1, v11 = v01 + 1;
+  auto ld = [&](int node, dfloat& x, dfloat& y) {
+    const double2 v = *reinterpret_cast<const double2*>(u + 2 * (size_t)node);
+    x = dfloat(v.x);
+    y = dfloat(v.y);
+  };
+  dfloat x00, y00, x10, y10, x01, y01, x11, y11;
+  ld(v00, x00, y00);
+  ld(v10, x10, y10);
+  ld(v01, x01, y01);
+  ld(v11, x11, y11);
+  const int e = cell * NE;
+  auto e0 = [&](int t) { return eig ? dfloat(eig[cj * NE + t]) : dfloat(0); };
+  const bool eg = eig != nullptr;
+  if constexpr (KIND == CROSSED) {
+    dfloat xc, yc;
+    ld(g.nv + cell, xc, yc);
+    q_elem_df<KIND, 0>(cs, lam2, c2, {x00, x10, xc}, {y00, y10, yc}, e0(0), eg, q, w64, w32, e);
+    q_elem_df<KIND, 1>(cs, lam2, c2, {x10, x11, xc}, {y10, y11, yc}, e0(1), eg, q, w64, w32, e + 1);
+    q_elem_df<KIND, 2>(cs, lam2, c2, {x11, x01, xc}, {y11, y01, yc}, e0(2), eg, q, w64, w32, e + 2);
+    q_elem_df<KIND, 3>(cs, lam2, c2, {x01, x00, xc}, {y01, y00, yc}, e0(3), eg, q, w64, w32, e + 3);
+  } else {
+    q_elem_df<KIND, 0>(cs, lam2, c2, {x00, x10, x11}, {y00, y10, y11}, e0(0), eg, q, w64, w32, e);
+    q_elem_df<KIND, 1>(cs, lam2, c2, {x00, x11, x01}, {y00, y11, y01}, e0(1), eg, q, w64, w32, e + 1);
+  }
+}
+
 void damage_q(cudaStream_t s, const Grid& g, const Mat& m, const double* u, const double* eig,
-              double* q, double* w64, float* w32) {
-  PF_LAUNCH(kclass(KC_SETUP, false, false), 0.0, s, pdl_launch(k_damage_q, nblocks(g.ncell), RED_THREADS, 0, s, g, m, u, eig, q, w64, w32));
+              double* q, double* w64, float* w32, bool df) {
+  if (df) {
+    const Consts<dfloat> cs = make_consts<dfloat>(g, m);
+    const dfloat lam2(2.0 * m.lam), c2(m.c2);
+    if (g.kind == CROSSED)
+      PF_LAUNCH(kclass(KC_DM_Q_DF, true, 0), 0.0, s, pdl_launch(k_damage_q_df<CROSSED>, nblocks(g.ncell), RED_THREADS, 0, s, g, cs, lam2, c2, u, eig, q, w64, w32));
+    else
+      PF_LAUNCH(kclass(KC_DM_Q_DF, true, 0), 0.0, s, pdl_launch(k_damage_q_df<RIGHT>, nblocks(g.ncell), RED_THREADS, 0, s, g, cs, lam2, c2, u, eig, q, w64, w32));
+    return;
+  }
+  PF_LAUNCH(kclass(KC_DM_Q, true, 0), 0.0, s, pdl_launch(k_damage_q, nblocks(g.ncell), RED_THREADS, 0, s, g, m, u, eig, q, w64, w32));
 }
 
 __global__ void k_energy(Grid g, Mat m, const double* u, const double* alpha, const double* eig,

@@ -69,7 +69,7 @@ const char* BASE_NAMES[KC_BASE_COUNT] = {
     "damage_apply", "damage_masked", "damage_resb", "damage_cheb", "damage_grad", "damage_trial",
     "vector", "reduce", "transfer", "setup", "coarse_solve", "tail_vcycle",
     "elastic_resid_df", "damage_grad_df", "damage_trial_df",
-    "elastic_cheb_z", "damage_cheb_z", "elastic_resb_z", "damage_resb_z"};
+    "elastic_cheb_z", "damage_cheb_z", "elastic_resb_z", "damage_resb_z", "damage_q", "damage_q_df"};
 
 }  // namespace
 

@@ -21,6 +21,7 @@ enum KernelClass : int {
   // smoothing from zero: the first (pointwise) Chebyshev step formed inside the second one's
   // launch, or inside the residual's when it is the only pre-smoothing step
   KC_EL_CHEB_Z, KC_DM_CHEB_Z, KC_EL_RESB_Z, KC_DM_RESB_Z,
+  KC_DM_Q, KC_DM_Q_DF,  // element energy densities of the damage operator: FP64, double-float
   KC_BASE_COUNT
 };
 // class id = base + KC_BASE_COUNT * (precision * KC_LEVELS + multigrid level), so that one class

@@ -1006,7 +1006,7 @@ pf_status trial_at(pf_sim& s, cudaStream_t st, const double* x, const double* d,
 void damage_prepare(pf_sim& s, cudaStream_t st, bool mixed) {
   const Grid& g = s.lv[0].g;
   damage_q(st, g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, s.lv[0].f64.wD,
-           mixed ? s.lv[0].f32.wD : nullptr);
+           mixed ? s.lv[0].f32.wD : nullptr, s.df);
   if (mixed) setup_damage<float>(s, st);
   else setup_damage<double>(s, st);
 }
@@ -1127,7 +1127,7 @@ pf_status energy_now(pf_sim& s, cudaStream_t st, double out[3]) {
 pf_status full_residual(pf_sim& s, cudaStream_t st, double zeta, double* nrm) {
   double rn;
   TRY(physical_residual(s, st, s.u, s.r64, &rn));
-  damage_q(st, s.lv[0].g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, nullptr, nullptr);
+  damage_q(st, s.lv[0].g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, nullptr, nullptr, s.df);
   double v[2];
   TRY(grad_at(s, st, s.alpha, zeta, s.Ftr, s.Phitr, s.rhstr, s.acttr, v));
   *nrm = sqrt(rn * rn + v[0]);
@@ -1378,7 +1378,7 @@ pf_status coupled_residual(pf_sim& s, cudaStream_t st, double zeta, double* nrm)
   double rn;
   TRY(physical_residual(s, st, s.u, s.r64, &rn));
   damage_q(st, s.lv[0].g, s.m, s.u, s.thermal ? s.eig : nullptr, s.q, s.lv[0].f64.wD,
-           s.lv[0].f32.wD);
+           s.lv[0].f32.wD, s.df);
   double v[2];
   TRY(grad_at(s, st, s.alpha, zeta, s.F, s.Phi, s.rhs, s.act, v));
   *nrm = sqrt(rn * rn + v[0]);
@@ -2176,9 +2176,10 @@ pf_status pf_op_damage_gradient(pf_sim* s, int precision, double* F, double* Phi
   if (!s->have_material) return fail(PF_EINVAL, "material not set");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
-  damage_q(st, s->lv[0].g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, nullptr, nullptr);
-  double v[2];
   s->df = precision == PF_MIXED;
+  damage_q(st, s->lv[0].g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, nullptr, nullptr,
+           s->df);
+  double v[2];
   TRY(grad_at(*s, st, s->alpha, 1e-10, F, Phi, s->rhstr, active ? active : s->acttr, v));
   if (phi_norm2) *phi_norm2 = v[0];
   return PF_OK;
@@ -2191,7 +2192,8 @@ pf_status pf_op_damage_apply(pf_sim* s, int precision, const void* x, void* y, v
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CU(cudaSetDevice(s->ctx->device));
   const Grid& g = s->lv[0].g;
-  damage_q(st, g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, s->lv[0].f64.wD, s->lv[0].f32.wD);
+  damage_q(st, g, s->m, s->u, s->thermal ? s->eig : nullptr, s->q, s->lv[0].f64.wD, s->lv[0].f32.wD,
+           precision == PF_MIXED);
   if (precision == PF_FP64) {
     DamageArgs<double> a{};
     a.x = static_cast<const double*>(x);
