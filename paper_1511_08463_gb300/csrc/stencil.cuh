@@ -48,9 +48,10 @@ inline Consts<T> make_consts(const Grid& g, const Mat& m) {
 // generic tile kernel
 // ----------------------------------------------------------------------------------------------
 // FP32 elasticity and damage operators are compiled for full occupancy (2048 threads per SM, at
-// most 32 registers per thread)
+// most 32 registers per thread), the double-float ones for half (at most 64 registers)
 template <class Op, int TYV = TY>
-__global__ void __launch_bounds__(TX* TYV, Op::FULL_OCC ? 2048 / (TX * TYV) : 1)
+__global__ void __launch_bounds__(TX* TYV, Op::FULL_OCC ? 2048 / (TX * TYV)
+                                                        : (Op::HALF_OCC ? 1024 / (TX * TYV) : 1))
     stencil_kernel(Op op) {
   pdl_enter();
   using V = typename Op::V;
@@ -297,6 +298,7 @@ template <class T, int KIND_, int COEF, int MODE, bool EIGEN, bool DOT, class C 
 struct ElasticOp {
   using Scalar = T;
   static constexpr bool FULL_OCC = sizeof(T) == 4;
+  static constexpr bool HALF_OCC = std::is_same<C, dfloat>::value;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_RESID || DOT) ? 1 : 0;
   static constexpr bool RED_MAX = false;
@@ -499,6 +501,7 @@ template <class T, int KIND_, int MODE, bool DOT, class C = T>
 struct DamageOp {
   using Scalar = T;
   static constexpr bool FULL_OCC = sizeof(T) == 4;
+  static constexpr bool HALF_OCC = std::is_same<C, dfloat>::value;
   static constexpr int KIND = KIND_;
   static constexpr int NR = (MODE == M_GRAD || MODE == M_TRIAL) ? 2 : (DOT ? 1 : 0);
   static constexpr bool RED_MAX = false;
@@ -689,6 +692,7 @@ template <class T, int KIND_, bool TRANSPOSE>
 struct CouplingOp {
   using Scalar = T;
   static constexpr bool FULL_OCC = false;
+  static constexpr bool HALF_OCC = false;
   static constexpr int KIND = KIND_;
   static constexpr int NR = 0;
   static constexpr bool RED_MAX = false;
