@@ -8,8 +8,10 @@
 // dense coarsest solve, then prolongation and post-smoothing back up -- with block barriers
 // between the steps instead of kernel boundaries.  Same operations as the grid-wide path (the
 // l1-Jacobi Chebyshev smoother on [0.1, 1], P1 transfers, masks for prescribed and active dofs,
-// coarsest solve with the stored inverse); operators are applied in gather form per node, so
-// sums run in a different order than in the tiled kernels.  FP32 only.
+// coarsest solve with the stored inverse, the Chebyshev coefficients the host computed for it);
+// operators are applied in gather form per node, so sums run in a different order than in the
+// tiled kernels.  Given the finer level's residual, the kernel forms its own right-hand side by
+// restriction as it loads the level.  FP32 only.
 #include "kernels.cuh"
 #include "mg_core.cuh"
 

@@ -42,3 +42,19 @@ def test_single_process_aggregate_is_identity():
     import bench
 
     assert bench.aggregate_max(3.25) == 3.25
+
+
+def test_select_steps_holds_the_growth_steps():
+    import bench
+
+    growth = (33, 34, 35, 36)
+    # the driver's sample: 20 of the steps after 5 warm-up steps, growth steps always in it
+    t = bench.select_steps(50, 5, 20, growth)
+    assert len(t) == 20 and all(s - 1 in t for s in growth)
+    assert t == sorted(t) and t[0] >= 5 and t[-1] <= 49
+    # a budget covering the range times all of it
+    assert bench.select_steps(50, 3, 47, growth) == list(range(3, 50))
+    # no growth steps: one timed step is the first after the warm-up
+    assert bench.select_steps(50, 3, 1, ()) == [3]
+    # fewer steps than growth steps: the first ones of them
+    assert bench.select_steps(50, 5, 2, growth) == [32, 33]
