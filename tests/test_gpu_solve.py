@@ -215,3 +215,27 @@ def test_load_exactly_at_damage_threshold_converges(precision):
         assert rep["status"] == 0 and rep["am_iters"] < 50
         assert rep["alpha_notconv"] == 0
     assert abs(rep["energy"][0] - 0.375) < 1e-4 and rep["energy"][1] < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_smoother_degree_one_matches_default(precision):
+    """With one pre-smoothing step per level, the step from zero is formed inside the residual
+    launch (grid levels) or pointwise (single-block tail): the multigrid changes, the converged load
+    steps do not.  Degree 1 on every level, with and without the tail, against the default."""
+    need_gpu()
+    from paper_1511_08463_gb300 import sim as S
+
+    w = W.notched_square(n=48, n_steps=6, t_max=1.5)
+    out = []
+    for deg, cdeg, tail in ((2, 0, 1), (1, 1, 1), (1, 1, 0)):
+        g = S.Sim(w)
+        o = tight_opts(S, omega=w.omega, precision=precision, mg_degree=deg, mg_coarse_degree=cdeg,
+                       mg_tail=tail)
+        for (t, dT) in w.loads:
+            r = g.load_step(t, dT, o)
+            assert r["status"] == 0
+        out.append((r["energy"][2], g.get_fields()))
+    for e, f in out[1:]:
+        assert abs(e - out[0][0]) <= 1e-8 * abs(out[0][0])
+        assert rel_max(f[0], out[0][1][0]) <= 1e-6
+        assert np.abs(f[1] - out[0][1][1]).max() <= 1e-6
