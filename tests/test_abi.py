@@ -126,3 +126,21 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert out.stdout.startswith("libpf")
+
+
+def test_kernel_class_names(lib):
+    """Launch-accounting classes (host-side table): one name per (kernel, precision, level), and
+    the names bench.py reads for its roofline and its double-float vs FP64 comparison exist."""
+    n = lib.pf_prof_class_count()
+    names = []
+    for k in range(n):
+        nm = C.c_char_p()
+        assert lib.pf_prof_get(k, C.byref(nm), None, None, None, None) == 0
+        names.append(nm.value.decode())
+    assert len(set(names)) == n
+    for want in ("elastic_cheb_f32_l0", "elastic_cheb_z_f32_l0", "tail_vcycle_f32_l6",
+                 "elastic_resid_df_f64_l0", "elastic_resid_f64_l0", "damage_grad_df_f64_l0",
+                 "damage_grad_f64_l0", "damage_trial_df_f64_l0", "damage_trial_f64_l0",
+                 "damage_q_df_f64_l0", "damage_q_f64_l0"):
+        assert want in names, want
+    assert lib.pf_prof_get(n, None, None, None, None, None) != 0
